@@ -1,0 +1,195 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) D2Q9 lid-driven cavity library.
+ *
+ * The method is the lattice Boltzmann scheme of Xiang & Shi, "Flow Simulation of Lid-Driven
+ * Rectangular Cavity by Using Lattice Boltzmann Method" (arXiv 2211.05009):
+ *   Sec. 2.1  Eq. 1 (BGK collision + streaming), Eq. 2 (equilibrium), Eq. 3 (moments),
+ *             Eq. 5 (nu = c_s^2 (tau - 1/2) dt);
+ *   Sec. 2.2  (i) initial state, (ii) non-equilibrium-extrapolation walls and moving lid,
+ *             (iii) Eq. 6 steady-state criterion;
+ *   Sec. 3    c = 1, dx = dt = 1, lid speed U; Table 1 / Table 2 stream-function post-processing;
+ *   Sec. 3.3  observing-point time series.
+ *
+ * Geometry: nx nodes along x (the cavity width L = nx), ny nodes along y (height, ny = nx*Ar).
+ * The walls are the outer ring of nodes (x = 0, x = nx-1, y = 0, y = ny-1); the lid is the top
+ * row y = ny-1 and moves along +x.  Fields exchanged through this ABI are row-major
+ * [ny][nx] FP64 with y = 0 at the bottom; population fields are [9][ny][nx] FP64 in the
+ * velocity order 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
+ *
+ * Conventions for every call:
+ *  - The return value is LBM_OK (0) or one of the LBM_E* codes below; lbm_last_error() gives the
+ *    detail.  No call aborts the process, traps on the GPU or prints.
+ *  - The context owns its device state (populations, velocity snapshot, reduction scratch).
+ *    Output buffers belong to the caller.  A "buffer" argument may be device memory, or host
+ *    memory (pageable or pinned); the library finds out which and copies as needed.
+ *  - Work is queued on the context's CUDA stream (lbm_set_stream; default: the legacy stream)
+ *    and calls return without waiting, except the ones documented as synchronising (those that
+ *    return host scalars, and any call given host buffers).
+ *  - One host thread at a time per context.  Contexts are independent.
+ *  - There is no CPU fallback: without a usable CUDA device lbm_create returns LBM_ECUDA.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ codes and types */
+#define LBM_OK 0
+#define LBM_EINVAL 1    /* bad argument: nx or ny < 3, tau <= 1/2, NULL where not allowed ...   */
+#define LBM_ENOMEM 2    /* device or host allocation failed (allocator hook included)           */
+#define LBM_ECUDA 3     /* a CUDA runtime call failed; the message names it                     */
+#define LBM_EDIVERGED 4 /* the mass or the Eq. 6 residual became NaN or Inf                      */
+#define LBM_ETIMEOUT 5  /* a bounded device-side wait ran out                                    */
+#define LBM_ENOTREADY 6 /* the value does not exist yet (no residual before the first 100 steps) */
+#define LBM_EIO 7       /* checkpoint file could not be written, read or did not match          */
+
+/* Storage type of the populations.  Arithmetic is FP64 for LBM_F64 and FP32 otherwise.
+ * The *S types store the shifted deviation g_j = f_j - w_j instead of f_j. */
+typedef enum {
+    LBM_F64 = 0,   /* f_j in FP64                                          */
+    LBM_F32 = 1,   /* f_j in FP32                                          */
+    LBM_F32S = 2,  /* g_j = f_j - w_j in FP32                              */
+    LBM_F16S = 3,  /* g_j in IEEE binary16                                 */
+    LBM_BF16S = 4  /* g_j in bfloat16                                      */
+} lbm_dtype;
+
+/* lbm_create_ex flags */
+#define LBM_FLAG_LID_CORNERS_MOVING 1u /* the two top corner nodes move with the lid (default: at rest) */
+
+#define LBM_MAX_PROBES 4
+#define LBM_RESIDUAL_INTERVAL 100 /* Eq. 6 compares velocity fields 100 steps apart */
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef struct {
+    int nx, ny;          /* nodes, walls included                                     */
+    long pitch;          /* device row pitch in elements (>= nx)                      */
+    double tau;          /* relaxation time of Eq. 1                                  */
+    double nu;           /* (tau - 1/2)/3, Eq. 5                                      */
+    double U;            /* lid speed                                                 */
+    double Re;           /* U nx / nu                                                 */
+    int dtype;           /* lbm_dtype                                                 */
+    unsigned flags;      /* LBM_FLAG_*                                                */
+    long step;           /* time steps taken since the state was initialised/loaded   */
+    size_t device_bytes; /* device memory the context holds                           */
+} lbm_info;
+
+/* ------------------------------------------------------------------ lifetime */
+
+/* Create a cavity of nx x ny nodes for Reynolds number Re = U L / nu with L = nx (Sec. 1) and
+ * lid speed U_lid (Sec. 2.2 ii); nu = U nx / Re and tau = 3 nu + 1/2 (Eq. 5, c_s^2 = 1/3).
+ * The state is initialised per Sec. 2.2 (i): rho = 1, u = 0 except u_x = U on the lid, f = f^eq.
+ * Errors: LBM_EINVAL (nx < 3, ny < 3, Re <= 0, tau <= 1/2, out == NULL, unknown dtype),
+ * LBM_ENOMEM, LBM_ECUDA.  On failure *out is NULL and lbm_last_error(NULL) holds the reason. */
+int lbm_create(int nx, int ny, double Re, double U_lid, lbm_dtype dtype, lbm_ctx **out);
+
+/* As lbm_create with tau given directly and LBM_FLAG_* flags. */
+int lbm_create_ex(int nx, int ny, double tau, double U_lid, lbm_dtype dtype, unsigned flags,
+                  lbm_ctx **out);
+
+/* Release everything the context holds (waits for its queued work).  NULL is a no-op. */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Message of the last failed call on ctx, or of the last failed lbm_create* on this thread when
+ * ctx is NULL.  Valid until the next call on the same context/thread. Never NULL. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Queue all later work of ctx on the given cudaStream_t (e.g. PyTorch's current stream).
+ * NULL selects the legacy default stream.  Waits for work already queued on the old stream. */
+int lbm_set_stream(lbm_ctx *ctx, void *cuda_stream);
+
+/* Device allocator hook used by every later lbm_create*: alloc(bytes, user) returns device
+ * memory or NULL (-> LBM_ENOMEM); release(ptr, user) frees it.  Pass NULLs for cudaMalloc. */
+int lbm_set_allocator(void *(*alloc)(size_t bytes, void *user),
+                      void (*release)(void *ptr, void *user), void *user);
+
+int lbm_get_info(const lbm_ctx *ctx, lbm_info *info);
+
+/* ------------------------------------------------------------------ the time step */
+
+/* Advance n >= 0 time steps of Eq. 1 with the Sec. 2.2 (ii) walls: for every node pull
+ * f_j(x - c_j) (streaming), form rho and u (Eq. 3) and collide towards f^eq (Eq. 2); wall nodes
+ * take f^eq(rho_f, u_w) + (1 - 1/tau)[f(x_f) - f^eq(rho_f, u_f)] from their inner neighbour
+ * x_f.  One fused kernel per step.  After every step whose global index is a multiple of 100
+ * the library also forms, in FP64, the mass sum rho and the Eq. 6 residual against the velocity
+ * field of 100 steps earlier, and samples the probes (lbm_probe).  Asynchronous.
+ * Errors: LBM_EINVAL (n < 0), LBM_ECUDA. */
+int lbm_step(lbm_ctx *ctx, long n);
+
+/* Run until the Eq. 6 residual (checked every 100 steps) drops below tol, or max_steps steps
+ * have been taken.  *steps_done (may be NULL) receives the steps taken in this call; the
+ * residual check lags one 100-step chunk behind the GPU, so up to 100 steps past the converged
+ * one may run.  Synchronising.  Returns LBM_OK when converged, LBM_ENOTREADY when max_steps ran
+ * out first, LBM_EDIVERGED on NaN/Inf. */
+int lbm_run_to_residual(lbm_ctx *ctx, double tol, long max_steps, long *steps_done);
+
+/* ------------------------------------------------------------------ observables */
+
+/* Macroscopic fields (Eq. 3) of the current state into caller buffers [ny][nx] FP64, any of
+ * which may be NULL.  Wall nodes report (rho_f, u_w), the moments their populations carry. */
+int lbm_moments(lbm_ctx *ctx, double *rho, double *ux, double *uy);
+
+/* Replace the state by f = f^eq(rho, u) node by node (Sec. 2.2 i generalised to a given field,
+ * e.g. a warm start).  Inputs [ny][nx] FP64; resets the step count and the Eq. 6 snapshot. */
+int lbm_set_moments(lbm_ctx *ctx, const double *rho, const double *ux, const double *uy);
+
+/* Current post-collision populations as FP64 f_j (not deviations), [9][ny][nx]. */
+int lbm_get_populations(lbm_ctx *ctx, double *f);
+
+/* Replace the populations (FP64 f_j, [9][ny][nx]); rounded to the storage type.  The step count
+ * and snapshot are kept.  Non-finite input is accepted and shows up as LBM_EDIVERGED later. */
+int lbm_set_populations(lbm_ctx *ctx, const double *f);
+
+/* Eq. 6 residual of the latest 100-step pair (host scalar, synchronising).
+ * LBM_ENOTREADY before the first 100 steps; LBM_EDIVERGED (and *r = NaN) if non-finite. */
+int lbm_residual(lbm_ctx *ctx, double *r);
+
+/* Total mass sum_x rho(x) of the current state, reduced in FP64 (host scalar, synchronising).
+ * LBM_EDIVERGED if non-finite. */
+int lbm_mass(lbm_ctx *ctx, double *m);
+
+/* Stream function of the current state with u_x = dPsi/dy, Psi = 0 on the bottom wall and the
+ * trapezoid rule in y (dy = 1), integrated in FP64 (the Psi of Table 1 / Table 2, with the sign
+ * that makes the primary vortex a minimum; the paper prints -Psi, Table 1 also divided by U nx).
+ * psi: optional [ny][nx] FP64 buffer (NULL: not stored).  psi_min (host) receives the minimum,
+ * xc / yc its node as x/nx and y/nx (width units, as in Table 1).  Synchronising. */
+int lbm_stream_function(lbm_ctx *ctx, double *psi, double *psi_min, double *xc, double *yc);
+
+/* Extrema of Psi restricted to the node window [i0, i1) x [j0, j1) (for secondary vortices,
+ * Table 1), with node indices.  Any output pointer may be NULL.  Synchronising. */
+int lbm_stream_function_window(lbm_ctx *ctx, int i0, int i1, int j0, int j1, double *psi_min,
+                               int *imin, int *jmin, double *psi_max, int *imax, int *jmax);
+
+/* Add an observing point (Sec. 3.3) at (x, y) in width units from the bottom-left corner, i.e.
+ * node (floor(x nx + 1/2), floor(y nx + 1/2)) clamped into the grid.  After every step t with
+ * t % every == 0 the velocity (u_x, u_y) of that node is written as two FP64 values to
+ * dev_series[2 k], dev_series[2 k + 1] with k = (sample number) mod cap; dev_series is a
+ * caller-owned DEVICE buffer of 2*cap doubles that must outlive the probe.  Returns the probe
+ * index (>= 0) or a negative LBM_E* code (LBM_EINVAL: every < 1, cap < 1, more than
+ * LBM_MAX_PROBES probes, dev_series not device memory). */
+int lbm_probe(lbm_ctx *ctx, double x, double y, int every, double *dev_series, long cap);
+
+/* Samples written so far by probe p (may exceed cap when the ring wrapped). */
+int lbm_probe_count(lbm_ctx *ctx, int p, long *n);
+
+/* Remove all probes. */
+int lbm_probe_clear(lbm_ctx *ctx);
+
+/* ------------------------------------------------------------------ checkpoint */
+
+/* Write / read the complete state (header with nx, ny, dtype, tau, U, flags, step; the stored
+ * populations; the Eq. 6 snapshot and last results).  lbm_load requires a file written for the
+ * same nx, ny and dtype (LBM_EIO otherwise).  A run continued from a checkpoint is bitwise
+ * identical to an uninterrupted one.  Synchronising. */
+int lbm_save(lbm_ctx *ctx, const char *path);
+int lbm_load(lbm_ctx *ctx, const char *path);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

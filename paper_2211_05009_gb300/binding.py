@@ -1,0 +1,233 @@
+"""Thin ctypes binding of the C ABI in ``include/lbm.h`` (argument marshalling only).
+
+Every function below has the name of the C entry point it calls and does no arithmetic of the
+method: all of it runs in the sm_103a kernels of ``liblbm.so``.  Buffers may be torch CUDA tensors
+(passed by device pointer), torch CPU tensors or numpy arrays (passed by host pointer).  Errors
+come back as :class:`LBMError` with the library's message.  There is no CPU fallback: if
+``liblbm.so`` has not been built, or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblbm.so")
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EDIVERGED, LBM_ETIMEOUT, LBM_ENOTREADY, LBM_EIO = range(8)
+ERROR_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_EDIVERGED",
+               5: "LBM_ETIMEOUT", 6: "LBM_ENOTREADY", 7: "LBM_EIO"}
+DTYPES = {"f64": 0, "f32": 1, "f32s": 2, "f16s": 3, "bf16s": 4}
+LBM_FLAG_LID_CORNERS_MOVING = 1
+LBM_MAX_PROBES = 4
+RESIDUAL_INTERVAL = 100
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class lbm_info(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("pitch", ctypes.c_long),
+                ("tau", ctypes.c_double), ("nu", ctypes.c_double), ("U", ctypes.c_double),
+                ("Re", ctypes.c_double), ("dtype", ctypes.c_int), ("flags", ctypes.c_uint),
+                ("step", ctypes.c_long), ("device_bytes", ctypes.c_size_t)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+
+# (name, restype, argtypes)
+_D, _I, _L, _P, _DP = ctypes.c_double, ctypes.c_int, ctypes.c_long, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+_SIGS = [
+    ("lbm_create", _I, [_I, _I, _D, _D, _I, ctypes.POINTER(_P)]),
+    ("lbm_create_ex", _I, [_I, _I, _D, _D, _I, ctypes.c_uint, ctypes.POINTER(_P)]),
+    ("lbm_destroy", None, [_P]),
+    ("lbm_last_error", ctypes.c_char_p, [_P]),
+    ("lbm_set_stream", _I, [_P, _P]),
+    ("lbm_set_allocator", _I, [ALLOC_FN, RELEASE_FN, _P]),
+    ("lbm_get_info", _I, [_P, ctypes.POINTER(lbm_info)]),
+    ("lbm_step", _I, [_P, _L]),
+    ("lbm_run_to_residual", _I, [_P, _D, _L, ctypes.POINTER(_L)]),
+    ("lbm_moments", _I, [_P, _P, _P, _P]),
+    ("lbm_set_moments", _I, [_P, _P, _P, _P]),
+    ("lbm_get_populations", _I, [_P, _P]),
+    ("lbm_set_populations", _I, [_P, _P]),
+    ("lbm_residual", _I, [_P, _DP]),
+    ("lbm_mass", _I, [_P, _DP]),
+    ("lbm_stream_function", _I, [_P, _P, _DP, _DP, _DP]),
+    ("lbm_stream_function_window", _I, [_P, _I, _I, _I, _I, _DP, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                         _DP, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    ("lbm_probe", _I, [_P, _D, _D, _I, _P, _L]),
+    ("lbm_probe_count", _I, [_P, _I, ctypes.POINTER(_L)]),
+    ("lbm_probe_clear", _I, [_P]),
+    ("lbm_save", _I, [_P, ctypes.c_char_p]),
+    ("lbm_load", _I, [_P, ctypes.c_char_p]),
+]
+EXPORTED = [s[0] for s in _SIGS]
+
+
+def library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load liblbm.so (built by ``paper_2211_05009_gb300.build``); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                               "(python -m paper_2211_05009_gb300.build); there is no CPU fallback")
+        lib = ctypes.CDLL(path)
+        for name, res, args in _SIGS:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _ptr(buf) -> int | None:
+    """Device or host address of a torch tensor / numpy array (contiguous), or None."""
+    if buf is None:
+        return None
+    if isinstance(buf, np.ndarray):
+        if not buf.flags.c_contiguous or buf.dtype != np.float64:
+            raise ValueError("numpy buffers must be C-contiguous float64")
+        return buf.ctypes.data
+    import torch
+    if isinstance(buf, torch.Tensor):
+        if not buf.is_contiguous() or buf.dtype != torch.float64:
+            raise ValueError("torch buffers must be contiguous float64")
+        return buf.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(buf)}")
+
+
+def _check(ctx, rc: int):
+    if rc != LBM_OK:
+        msg = library().lbm_last_error(ctx).decode(errors="replace")
+        raise LBMError(rc, msg)
+
+
+# ------------------------------------------------------------------ one wrapper per entry point
+def lbm_create(nx: int, ny: int, Re: float, U_lid: float, dtype: str | int = "f32s"):
+    out = ctypes.c_void_p()
+    rc = library().lbm_create(nx, ny, Re, U_lid, DTYPES.get(dtype, dtype), ctypes.byref(out))
+    _check(None, rc)
+    return out.value
+
+
+def lbm_create_ex(nx: int, ny: int, tau: float, U_lid: float, dtype: str | int = "f32s", flags: int = 0):
+    out = ctypes.c_void_p()
+    rc = library().lbm_create_ex(nx, ny, tau, U_lid, DTYPES.get(dtype, dtype), flags, ctypes.byref(out))
+    _check(None, rc)
+    return out.value
+
+
+def lbm_destroy(ctx) -> None:
+    library().lbm_destroy(ctx)
+
+
+def lbm_last_error(ctx) -> str:
+    return library().lbm_last_error(ctx).decode(errors="replace")
+
+
+def lbm_set_stream(ctx, stream_handle: int | None) -> None:
+    _check(ctx, library().lbm_set_stream(ctx, stream_handle))
+
+
+def lbm_set_allocator(alloc, release, user=None) -> None:
+    """alloc/release are ALLOC_FN/RELEASE_FN instances (keep them alive) or None for cudaMalloc."""
+    a = alloc if alloc is not None else ctypes.cast(None, ALLOC_FN)
+    r = release if release is not None else ctypes.cast(None, RELEASE_FN)
+    _check(None, library().lbm_set_allocator(a, r, user))
+
+
+def lbm_get_info(ctx) -> lbm_info:
+    info = lbm_info()
+    _check(ctx, library().lbm_get_info(ctx, ctypes.byref(info)))
+    return info
+
+
+def lbm_step(ctx, n: int) -> None:
+    _check(ctx, library().lbm_step(ctx, int(n)))
+
+
+def lbm_run_to_residual(ctx, tol: float, max_steps: int) -> tuple[int, int]:
+    """Returns (return code, steps taken): LBM_OK when converged, LBM_ENOTREADY when the step
+    budget ran out; other codes raise."""
+    done = ctypes.c_long(0)
+    rc = library().lbm_run_to_residual(ctx, float(tol), int(max_steps), ctypes.byref(done))
+    if rc not in (LBM_OK, LBM_ENOTREADY):
+        _check(ctx, rc)
+    return rc, done.value
+
+
+def lbm_moments(ctx, rho=None, ux=None, uy=None) -> None:
+    _check(ctx, library().lbm_moments(ctx, _ptr(rho), _ptr(ux), _ptr(uy)))
+
+
+def lbm_set_moments(ctx, rho, ux, uy) -> None:
+    _check(ctx, library().lbm_set_moments(ctx, _ptr(rho), _ptr(ux), _ptr(uy)))
+
+
+def lbm_get_populations(ctx, f) -> None:
+    _check(ctx, library().lbm_get_populations(ctx, _ptr(f)))
+
+
+def lbm_set_populations(ctx, f) -> None:
+    _check(ctx, library().lbm_set_populations(ctx, _ptr(f)))
+
+
+def lbm_residual(ctx) -> float:
+    r = ctypes.c_double()
+    _check(ctx, library().lbm_residual(ctx, ctypes.byref(r)))
+    return r.value
+
+
+def lbm_mass(ctx) -> float:
+    m = ctypes.c_double()
+    _check(ctx, library().lbm_mass(ctx, ctypes.byref(m)))
+    return m.value
+
+
+def lbm_stream_function(ctx, psi=None) -> tuple[float, float, float]:
+    vmin, xc, yc = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(ctx, library().lbm_stream_function(ctx, _ptr(psi), ctypes.byref(vmin), ctypes.byref(xc), ctypes.byref(yc)))
+    return vmin.value, xc.value, yc.value
+
+
+def lbm_stream_function_window(ctx, i0: int, i1: int, j0: int, j1: int):
+    vmin, vmax = ctypes.c_double(), ctypes.c_double()
+    imin, jmin, imax, jmax = (ctypes.c_int() for _ in range(4))
+    _check(ctx, library().lbm_stream_function_window(ctx, i0, i1, j0, j1, ctypes.byref(vmin), ctypes.byref(imin),
+                                                     ctypes.byref(jmin), ctypes.byref(vmax), ctypes.byref(imax),
+                                                     ctypes.byref(jmax)))
+    return (vmin.value, imin.value, jmin.value), (vmax.value, imax.value, jmax.value)
+
+
+def lbm_probe(ctx, x: float, y: float, every: int, dev_series, cap: int) -> int:
+    q = library().lbm_probe(ctx, float(x), float(y), int(every), _ptr(dev_series), int(cap))
+    if q < 0:
+        _check(ctx, -q)
+    return q
+
+
+def lbm_probe_count(ctx, p: int) -> int:
+    n = ctypes.c_long()
+    _check(ctx, library().lbm_probe_count(ctx, p, ctypes.byref(n)))
+    return n.value
+
+
+def lbm_probe_clear(ctx) -> None:
+    _check(ctx, library().lbm_probe_clear(ctx))
+
+
+def lbm_save(ctx, path: str) -> None:
+    _check(ctx, library().lbm_save(ctx, path.encode()))
+
+
+def lbm_load(ctx, path: str) -> None:
+    _check(ctx, library().lbm_load(ctx, path.encode()))

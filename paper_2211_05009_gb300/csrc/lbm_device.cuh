@@ -1,0 +1,115 @@
+// lbm_device.cuh -- device-side building blocks of the sm_103a D2Q9 cavity library.
+//
+// Method: Xiang & Shi (arXiv 2211.05009) Sec. 2.1 Eq. 1-3, Eq. 5 and Sec. 2.2 (i)-(iii).
+// Storage: SoA f[q][ny][pitch]; rows are 128-byte multiples and a warp owns 32*V consecutive
+// nodes of one row, so every population is read and written with one 16-byte vector access per
+// thread.  The +-1 x neighbours of a pull come from the adjacent lane by warp shuffle.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// D2Q9 velocity set and weights, Sec. 2.1 (after Eq. 2), c = 1 (Sec. 3).
+// Order: 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
+__host__ __device__ constexpr int cx(int j) { return j == 1 || j == 5 || j == 8 ? 1 : (j == 3 || j == 6 || j == 7 ? -1 : 0); }
+__host__ __device__ constexpr int cy(int j) { return j == 2 || j == 5 || j == 6 ? 1 : (j == 4 || j == 7 || j == 8 ? -1 : 0); }
+__host__ __device__ constexpr double wd(int j) { return j == 0 ? 4.0 / 9.0 : (j < 5 ? 1.0 / 9.0 : 1.0 / 36.0); }
+
+constexpr int kMaxProbes = 4;
+constexpr int kInterval = 100;  // Eq. 6 compares fields 100 steps apart
+
+// ------------------------------------------------------------------ storage traits
+// V = nodes per 16-byte vector; C = arithmetic type.
+template <typename S> struct St;
+template <> struct St<double> {
+    static constexpr int V = 2;
+    using C = double;
+    __device__ static double to(double v) { return v; }
+    __device__ static double from(double v) { return v; }
+};
+template <> struct St<float> {
+    static constexpr int V = 4;
+    using C = float;
+    __device__ static float to(float v) { return v; }
+    __device__ static float from(float v) { return v; }
+};
+template <> struct St<__half> {
+    static constexpr int V = 8;
+    using C = float;
+    __device__ static float to(__half v) { return __half2float(v); }
+    __device__ static __half from(float v) { return __float2half_rn(v); }
+};
+template <> struct St<__nv_bfloat16> {
+    static constexpr int V = 8;
+    using C = float;
+    __device__ static float to(__nv_bfloat16 v) { return __bfloat162float(v); }
+    __device__ static __nv_bfloat16 from(float v) { return __float2bfloat16_rn(v); }
+};
+
+// 16-byte vector load/store of V storage elements, converted to/from C.
+template <typename S>
+__device__ __forceinline__ void vload(const S* __restrict__ p, typename St<S>::C (&out)[St<S>::V]) {
+    constexpr int V = St<S>::V;
+    union { uint4 u; S s[V]; } b;
+    b.u = __ldg(reinterpret_cast<const uint4*>(p));
+#pragma unroll
+    for (int i = 0; i < V; ++i) out[i] = St<S>::to(b.s[i]);
+}
+template <typename S>
+__device__ __forceinline__ void vstore(S* __restrict__ p, const typename St<S>::C (&in)[St<S>::V]) {
+    constexpr int V = St<S>::V;
+    union { uint4 u; S s[V]; } b;
+#pragma unroll
+    for (int i = 0; i < V; ++i) b.s[i] = St<S>::from(in[i]);
+    *reinterpret_cast<uint4*>(p) = b.u;
+}
+
+// ------------------------------------------------------------------ arguments
+struct ProbeSet {
+    int n;
+    int px[kMaxProbes], py[kMaxProbes], every[kMaxProbes];
+    long long start[kMaxProbes];  // global step at which the probe was added
+    long long cap[kMaxProbes];
+    double* series[kMaxProbes];
+};
+
+// Device-resident state shared by every launch of a context.
+struct DevState {
+    long long base;       // global step index of the last 100-step checkpoint
+    double residual;      // Eq. 6 at the last checkpoint
+    double mass;          // sum rho at the last checkpoint
+    double num, den;      // Eq. 6 numerator / denominator
+    long long at_step;    // global step of that checkpoint
+    int valid;            // 1 once a checkpoint exists
+    int pad;
+    double scalar;        // result of the last on-demand reduction (mass)
+    double ext[6];        // stream-function window extrema: min, imin, jmin, max, imax, jmax
+};
+
+struct StepArgs {
+    const void* src;
+    void* dst;
+    int nx, ny;
+    long long pitch;  // elements per row
+    long long plane;  // pitch * ny
+    double omega;     // 1/tau
+    double U;         // lid speed
+    int corner_moving;
+    int s;            // steps since the last checkpoint (0..99) of the state being advanced
+    DevState* state;
+    ProbeSet probes;
+    double* snap;      // [2][ny][pitch] Eq. 6 snapshot (REDUCE only)
+    double* partials;  // [blocks][3]               (REDUCE only)
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace lbm

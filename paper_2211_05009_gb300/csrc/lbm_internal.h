@@ -1,0 +1,55 @@
+// lbm_internal.h -- declarations shared by the translation units of the CUDA library
+// (kernel launchers and the per-context state).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+struct StepGeometry {
+    int grid_x, grid_y, blocks;
+};
+
+// Geometry of the step launch (also the number of reduction partials).
+StepGeometry step_geometry(int dtype, int nx, int ny, long long pitch);
+
+// Row pitch (elements) for a storage type: a multiple of 32 lanes x 16 bytes.
+long long row_pitch(int dtype, int nx);
+int storage_bytes(int dtype);
+
+cudaError_t launch_step(int dtype, const StepArgs& a, bool reduce, cudaStream_t st);
+cudaError_t launch_finalize_checkpoint(const double* partials, int nblocks, double nodes,
+                                       DevState* st, cudaStream_t s);
+
+struct FieldArgs {
+    void* f;  // populations [9][ny][pitch] of the storage type
+    int nx, ny;
+    long long pitch, plane;
+    double U;
+    int corner_moving;
+};
+
+// f = f^eq(1, u0) with the Sec. 2.2 (i) initial velocity; snapshot = u0.
+cudaError_t launch_init(int dtype, const FieldArgs& a, double* snap, cudaStream_t st);
+// f = f^eq(rho, u) from dense [ny][nx] FP64 fields; snapshot = u.
+cudaError_t launch_set_moments(int dtype, const FieldArgs& a, const double* rho, const double* ux,
+                               const double* uy, double* snap, cudaStream_t st);
+// Dense [ny][nx] FP64 moments (any output may be null).
+cudaError_t launch_moments(int dtype, const FieldArgs& a, double* rho, double* ux, double* uy,
+                           cudaStream_t st);
+// Dense [9][ny][nx] FP64 populations <-> storage.
+cudaError_t launch_get_populations(int dtype, const FieldArgs& a, double* out, cudaStream_t st);
+cudaError_t launch_set_populations(int dtype, const FieldArgs& a, const double* in, cudaStream_t st);
+// Mass: sum over nodes of (rho - 1) into partials, then N + sum into st->scalar.
+cudaError_t launch_mass(int dtype, const FieldArgs& a, double* partials, int max_partials,
+                        DevState* state, cudaStream_t st);
+// Stream function (u_x = dPsi/dy, trapezoid in y from Psi = 0 at y = 0) with window extrema
+// into state->ext; psi (dense [ny][nx]) may be null.  scratch needs psi_scratch_doubles().
+size_t psi_scratch_doubles(int nx, int ny);
+cudaError_t launch_stream_function(int dtype, const FieldArgs& a, double* psi, int i0, int i1,
+                                   int j0, int j1, double* scratch, DevState* state,
+                                   cudaStream_t st);
+
+}  // namespace lbm
