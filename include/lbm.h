@@ -76,6 +76,7 @@ typedef struct {
     unsigned flags;      /* LBM_FLAG_*                                                */
     long step;           /* time steps taken since the state was initialised/loaded   */
     size_t device_bytes; /* device memory the context holds                           */
+    int launch_config;   /* launch shape of the step kernel (lbm_set_launch_config)   */
 } lbm_info;
 
 /* ------------------------------------------------------------------ lifetime */
@@ -121,11 +122,28 @@ int lbm_get_info(const lbm_ctx *ctx, lbm_info *info);
 int lbm_step(lbm_ctx *ctx, long n);
 
 /* Run until the Eq. 6 residual (checked every 100 steps) drops below tol, or max_steps steps
- * have been taken.  *steps_done (may be NULL) receives the steps taken in this call; the
- * residual check lags one 100-step chunk behind the GPU, so up to 100 steps past the converged
- * one may run.  Synchronising.  Returns LBM_OK when converged, LBM_ENOTREADY when max_steps ran
- * out first, LBM_EDIVERGED on NaN/Inf. */
+ * have been taken.  *steps_done (may be NULL) receives the steps taken in this call.  The host
+ * reads each checkpoint one 100-step chunk behind the GPU (no stall); it stops once two
+ * consecutive checkpoints are below tol, so the returned state itself satisfies the criterion
+ * (lbm_residual < tol).  Synchronising.  Returns LBM_OK when converged, LBM_ENOTREADY when
+ * max_steps ran out first, LBM_EDIVERGED on NaN/Inf. */
 int lbm_run_to_residual(lbm_ctx *ctx, double tol, long max_steps, long *steps_done);
+
+/* ------------------------------------------------------------------ launch shapes */
+
+/* The fused step kernel has several launch shapes (rows per thread, warps per block, register
+ * budget).  They compute bitwise-identical populations; only speed differs (the FP64 checkpoint
+ * sums may differ in the last bits, since the partial sums are grouped by block). */
+int lbm_launch_config_count(void);
+
+/* Select shape cfg in [0, lbm_launch_config_count()).  Synchronising.  LBM_EINVAL if out of range. */
+int lbm_set_launch_config(lbm_ctx *ctx, int cfg);
+
+/* Time every shape for steps_per_trial (>= 2) steps on a scratch context of the same size (the
+ * caller's state is not touched; the scratch needs as much device memory as ctx) and select the
+ * fastest.  *best / *best_glups (either may be NULL) receive the choice and its step rate in
+ * 1e9 lattice updates per second.  Synchronising. */
+int lbm_autotune(lbm_ctx *ctx, int steps_per_trial, int *best, double *best_glups);
 
 /* ------------------------------------------------------------------ observables */
 

@@ -35,7 +35,7 @@ class lbm_info(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("pitch", ctypes.c_long),
                 ("tau", ctypes.c_double), ("nu", ctypes.c_double), ("U", ctypes.c_double),
                 ("Re", ctypes.c_double), ("dtype", ctypes.c_int), ("flags", ctypes.c_uint),
-                ("step", ctypes.c_long), ("device_bytes", ctypes.c_size_t)]
+                ("step", ctypes.c_long), ("device_bytes", ctypes.c_size_t), ("launch_config", ctypes.c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -53,6 +53,9 @@ _SIGS = [
     ("lbm_set_stream", _I, [_P, _P]),
     ("lbm_set_allocator", _I, [ALLOC_FN, RELEASE_FN, _P]),
     ("lbm_get_info", _I, [_P, ctypes.POINTER(lbm_info)]),
+    ("lbm_launch_config_count", _I, []),
+    ("lbm_set_launch_config", _I, [_P, _I]),
+    ("lbm_autotune", _I, [_P, _I, ctypes.POINTER(_I), _DP]),
     ("lbm_step", _I, [_P, _L]),
     ("lbm_run_to_residual", _I, [_P, _D, _L, ctypes.POINTER(_L)]),
     ("lbm_moments", _I, [_P, _P, _P, _P]),
@@ -149,6 +152,20 @@ def lbm_get_info(ctx) -> lbm_info:
     info = lbm_info()
     _check(ctx, library().lbm_get_info(ctx, ctypes.byref(info)))
     return info
+
+
+def lbm_launch_config_count() -> int:
+    return library().lbm_launch_config_count()
+
+
+def lbm_set_launch_config(ctx, cfg: int) -> None:
+    _check(ctx, library().lbm_set_launch_config(ctx, int(cfg)))
+
+
+def lbm_autotune(ctx, steps_per_trial: int = 20) -> tuple[int, float]:
+    best, glups = ctypes.c_int(), ctypes.c_double()
+    _check(ctx, library().lbm_autotune(ctx, int(steps_per_trial), ctypes.byref(best), ctypes.byref(glups)))
+    return best.value, glups.value
 
 
 def lbm_step(ctx, n: int) -> None:

@@ -63,6 +63,7 @@ struct lbm_ctx {
     cudaEvent_t ev[2] = {nullptr, nullptr};
 
     ProbeSet probes{};
+    int cfg = kDefaultStepConfig;  // launch shape of the step kernel
     StepGeometry geo{};
     std::string err;
 
@@ -139,7 +140,7 @@ struct lbm_ctx {
     int enqueue_step(long long gstep, cudaStream_t st) {
         const int s = (int)(gstep % kInterval);
         const bool reduce = (gstep + 1) % kInterval == 0;
-        int rc = cuda(launch_step(dtype, step_args(gstep, s), reduce, st), "step kernel launch");
+        int rc = cuda(launch_step(dtype, cfg, step_args(gstep, s), reduce, st), "step kernel launch");
         if (rc) return rc;
         if (reduce) {
             rc = cuda(launch_finalize_checkpoint(partials, geo.blocks, (double)nx * ny, d_state, st),
@@ -286,7 +287,12 @@ extern "C" int lbm_create_ex(int nx, int ny, double tau, double U, lbm_dtype dty
     c->alloc_user = g_alloc_user;
     c->pitch = row_pitch(c->dtype, nx);
     c->plane = c->pitch * (long long)ny;
-    c->geo = step_geometry(c->dtype, nx, ny, c->pitch);
+    c->geo = step_geometry(c->dtype, c->cfg, ny, c->pitch);
+    int max_blocks = 0;
+    for (int k = 0; k < kStepConfigs; ++k) {
+        const int b = step_geometry(c->dtype, k, ny, c->pitch).blocks;
+        max_blocks = b > max_blocks ? b : max_blocks;
+    }
 
     const size_t pop_bytes = 9ull * (size_t)c->plane * (size_t)storage_bytes(c->dtype);
     int rc;
@@ -295,7 +301,7 @@ extern "C" int lbm_create_ex(int nx, int ny, double tau, double U, lbm_dtype dty
         if (!c->buf[b]) return create_fail(c, LBM_ENOMEM, fmt("population buffer of %zu bytes", pop_bytes));
     }
     c->snap = (double*)c->dalloc(2ull * (size_t)c->plane * sizeof(double));
-    c->npartials = 3 * c->geo.blocks > 4096 ? 3 * c->geo.blocks : 4096;
+    c->npartials = 3 * max_blocks > 4096 ? 3 * max_blocks : 4096;
     c->partials = (double*)c->dalloc((size_t)c->npartials * sizeof(double));
     c->psi_scratch = (double*)c->dalloc(psi_scratch_doubles(nx, ny) * sizeof(double));
     c->d_state = (DevState*)c->dalloc(sizeof(DevState));
@@ -357,7 +363,67 @@ extern "C" int lbm_get_info(const lbm_ctx* c, lbm_info* info) {
     info->flags = c->flags;
     info->step = (long)c->step;
     info->device_bytes = c->device_bytes;
+    info->launch_config = c->cfg;
     return LBM_OK;
+}
+
+extern "C" int lbm_launch_config_count(void) { return kStepConfigs; }
+
+extern "C" int lbm_set_launch_config(lbm_ctx* c, int cfg) {
+    if (!c) return LBM_EINVAL;
+    if (cfg < 0 || cfg >= kStepConfigs) return c->fail(LBM_EINVAL, fmt("launch config %d out of range", cfg));
+    int rc = c->sync();
+    if (rc) return rc;
+    c->cfg = cfg;
+    c->geo = step_geometry(c->dtype, cfg, c->ny, c->pitch);
+    c->invalidate_graphs();
+    return LBM_OK;
+}
+
+extern "C" int lbm_autotune(lbm_ctx* c, int steps_per_trial, int* best, double* best_glups) {
+    if (!c || steps_per_trial < 2) return c ? c->fail(LBM_EINVAL, "steps_per_trial < 2") : LBM_EINVAL;
+    // trials run on a scratch context of the same shape so the caller's state is untouched
+    void* (*sa)(size_t, void*) = g_alloc;
+    void (*sr)(void*, void*) = g_release;
+    void* su = g_alloc_user;
+    g_alloc = c->alloc;
+    g_release = c->release;
+    g_alloc_user = c->alloc_user;
+    lbm_ctx* t = nullptr;
+    int rc = lbm_create_ex(c->nx, c->ny, c->tau, c->U, (lbm_dtype)c->dtype, c->flags, &t);
+    g_alloc = sa;
+    g_release = sr;
+    g_alloc_user = su;
+    if (rc) return c->fail(rc, std::string("autotune scratch context: ") + lbm_last_error(nullptr));
+    t->stream = c->stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    rc = c->cuda(cudaEventCreate(&e0), "event create");
+    if (!rc) rc = c->cuda(cudaEventCreate(&e1), "event create");
+    int arg = -1;
+    float best_ms = 0.f;
+    for (int k = 0; k < kStepConfigs && !rc; ++k) {
+        // steps 0..97 of a checkpoint interval never reduce; warm up once, then time
+        for (int rep = 0; rep < 2 && !rc; ++rep) {
+            if (rep == 1) rc = c->cuda(cudaEventRecord(e0, t->stream), "event record");
+            for (int s = 0; s < steps_per_trial && !rc; ++s)
+                rc = c->cuda(launch_step(t->dtype, k, t->step_args(s & 1, s % 98), false, t->stream), "autotune launch");
+        }
+        if (!rc) rc = c->cuda(cudaEventRecord(e1, t->stream), "event record");
+        if (!rc) rc = c->cuda(cudaEventSynchronize(e1), "event synchronize");
+        float ms = 0.f;
+        if (!rc) rc = c->cuda(cudaEventElapsedTime(&ms, e0, e1), "event time");
+        if (!rc && (arg < 0 || ms < best_ms)) {
+            arg = k;
+            best_ms = ms;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    lbm_destroy(t);
+    if (rc) return rc;
+    if (best) *best = arg;
+    if (best_glups) *best_glups = (double)c->nx * c->ny * steps_per_trial / (best_ms * 1e-3) / 1e9;
+    return lbm_set_launch_config(c, arg);
 }
 
 // ------------------------------------------------------------------ stepping
@@ -410,8 +476,13 @@ extern "C" int lbm_run_to_residual(lbm_ctx* c, double tol, long max_steps, long*
             double r = 0;
             if (!rc) rc = read_checkpoint(c, pending, &r);
             if (!rc && r < tol) {
-                converged = true;
-                break;
+                // converged one chunk ago; the state returned must satisfy it too
+                rc = c->cuda(cudaEventSynchronize(c->ev[(at / kInterval) & 1]), "event synchronize");
+                if (!rc) rc = read_checkpoint(c, at, &r);
+                if (!rc && r < tol) {
+                    converged = true;
+                    break;
+                }
             }
         }
         pending = at;

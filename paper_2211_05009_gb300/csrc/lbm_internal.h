@@ -12,14 +12,18 @@ struct StepGeometry {
     int grid_x, grid_y, blocks;
 };
 
-// Geometry of the step launch (also the number of reduction partials).
-StepGeometry step_geometry(int dtype, int nx, int ny, long long pitch);
+// Launch shapes of the step kernel (see lbm_step_kernel.cuh); all give identical populations.
+constexpr int kStepConfigs = 6;
+constexpr int kDefaultStepConfig = 0;
+
+// Geometry of the step launch for a shape (also the number of reduction partials).
+StepGeometry step_geometry(int dtype, int cfg, int ny, long long pitch);
 
 // Row pitch (elements) for a storage type: a multiple of 32 lanes x 16 bytes.
 long long row_pitch(int dtype, int nx);
 int storage_bytes(int dtype);
 
-cudaError_t launch_step(int dtype, const StepArgs& a, bool reduce, cudaStream_t st);
+cudaError_t launch_step(int dtype, int cfg, const StepArgs& a, bool reduce, cudaStream_t st);
 cudaError_t launch_finalize_checkpoint(const double* partials, int nblocks, double nodes,
                                        DevState* st, cudaStream_t s);
 

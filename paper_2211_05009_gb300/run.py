@@ -1,0 +1,56 @@
+"""Command-line runner: one cavity, a fixed number of time steps, timing and observables.
+
+  python -m paper_2211_05009_gb300.run --nx 2048 --ny 2048 --re 8000 --u 0.05 --dtype f32s --steps 1000
+
+Prints one JSON line with the step rate (GLUPS from CUDA events on the library's stream), the
+Eq. 6 residual, the mass and the primary-vortex minimum of Psi with its centre.  Also the command
+the profiles under profiles/ were taken with.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import torch
+
+from . import binding as B
+from .build import build
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--nx", type=int, default=2048)
+    ap.add_argument("--ny", type=int, default=2048)
+    ap.add_argument("--re", type=float, default=8000.0)
+    ap.add_argument("--u", type=float, default=0.05)
+    ap.add_argument("--dtype", default="f32s", choices=sorted(B.DTYPES))
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=0)
+    a = ap.parse_args(argv)
+    build()
+    stream = torch.cuda.current_stream()
+    ctx = B.lbm_create(a.nx, a.ny, a.re, a.u, a.dtype)
+    try:
+        B.lbm_set_stream(ctx, stream.cuda_stream)
+        if a.warmup:
+            B.lbm_step(ctx, a.warmup)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        B.lbm_step(ctx, a.steps)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        sec = t0.elapsed_time(t1) / 1e3
+        out = {"nx": a.nx, "ny": a.ny, "Re": a.re, "U": a.u, "dtype": a.dtype, "steps": a.steps,
+               "seconds": sec, "glups": a.nx * a.ny * a.steps / sec / 1e9 if sec > 0 else None,
+               "mass": B.lbm_mass(ctx)}
+        if a.warmup + a.steps >= B.RESIDUAL_INTERVAL:
+            out["residual"] = B.lbm_residual(ctx)
+        out["psi_min"], out["xc"], out["yc"] = B.lbm_stream_function(ctx)
+        print(json.dumps(out), flush=True)
+    finally:
+        B.lbm_destroy(ctx)
+
+
+if __name__ == "__main__":
+    main()

