@@ -48,9 +48,9 @@ extern "C" {
 #define LBM_EIO 7       /* checkpoint file could not be written, read or did not match          */
 
 /* Storage type of the populations.  Arithmetic is FP64 for LBM_F64 and FP32 otherwise.
- * The *S types store the shifted deviation g_j = f_j - w_j instead of f_j. */
+ * The *S types (and LBM_F64) store the shifted deviation g_j = f_j - w_j instead of f_j. */
 typedef enum {
-    LBM_F64 = 0,   /* f_j in FP64                                          */
+    LBM_F64 = 0,   /* g_j = f_j - w_j in FP64                              */
     LBM_F32 = 1,   /* f_j in FP32                                          */
     LBM_F32S = 2,  /* g_j = f_j - w_j in FP32                              */
     LBM_F16S = 3,  /* g_j in IEEE binary16                                 */

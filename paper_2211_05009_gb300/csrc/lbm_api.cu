@@ -48,7 +48,7 @@ struct lbm_ctx {
     size_t device_bytes = 0;
 
     void* buf[2] = {nullptr, nullptr};  // populations, ping-pong; current = buf[step & 1]
-    double* snap = nullptr;             // [2][ny][pitch] Eq. 6 snapshot
+    void* snap = nullptr;               // [2][ny][pitch] Eq. 6 snapshot (arithmetic type)
     double* partials = nullptr;         // reduction partials
     int npartials = 0;
     double* psi_scratch = nullptr;
@@ -300,7 +300,7 @@ extern "C" int lbm_create_ex(int nx, int ny, double tau, double U, lbm_dtype dty
         c->buf[b] = c->dalloc(pop_bytes);
         if (!c->buf[b]) return create_fail(c, LBM_ENOMEM, fmt("population buffer of %zu bytes", pop_bytes));
     }
-    c->snap = (double*)c->dalloc(2ull * (size_t)c->plane * sizeof(double));
+    c->snap = c->dalloc(2ull * (size_t)c->plane * arith_bytes(c->dtype));
     c->npartials = 3 * max_blocks > 4096 ? 3 * max_blocks : 4096;
     c->partials = (double*)c->dalloc((size_t)c->npartials * sizeof(double));
     c->psi_scratch = (double*)c->dalloc(psi_scratch_doubles(nx, ny) * sizeof(double));
@@ -715,13 +715,14 @@ extern "C" int lbm_save(lbm_ctx* c, const char* path) {
     const size_t es = storage_bytes(c->dtype);
     const size_t row = (size_t)c->nx * es;
     const size_t pop_bytes = 9ull * c->ny * row;
-    const size_t snap_bytes = 2ull * c->ny * c->nx * sizeof(double);
+    const size_t ab = (size_t)arith_bytes(c->dtype);
+    const size_t snap_bytes = 2ull * c->ny * c->nx * ab;
     char* host = (char*)malloc(pop_bytes + snap_bytes + sizeof(DevState));
     if (!host) return c->fail(LBM_ENOMEM, "host buffer for checkpoint");
     int rc = c->cuda(cudaMemcpy2DAsync(host, row, c->buf[c->step & 1], (size_t)c->pitch * es, row,
                                        9ull * c->ny, cudaMemcpyDeviceToHost, c->stream), "population copy");
-    if (!rc) rc = c->cuda(cudaMemcpy2DAsync(host + pop_bytes, c->nx * sizeof(double), c->snap, (size_t)c->pitch * sizeof(double),
-                                            c->nx * sizeof(double), 2ull * c->ny, cudaMemcpyDeviceToHost, c->stream), "snapshot copy");
+    if (!rc) rc = c->cuda(cudaMemcpy2DAsync(host + pop_bytes, c->nx * ab, c->snap, (size_t)c->pitch * ab,
+                                            c->nx * ab, 2ull * c->ny, cudaMemcpyDeviceToHost, c->stream), "snapshot copy");
     if (!rc) rc = c->cuda(cudaMemcpyAsync(host + pop_bytes + snap_bytes, c->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream), "state copy");
     if (!rc) rc = c->sync();
     if (rc) {
@@ -762,7 +763,8 @@ extern "C" int lbm_load(lbm_ctx* c, const char* path) {
     const size_t es = storage_bytes(c->dtype);
     const size_t row = (size_t)c->nx * es;
     const size_t pop_bytes = 9ull * c->ny * row;
-    const size_t snap_bytes = 2ull * c->ny * c->nx * sizeof(double);
+    const size_t ab = (size_t)arith_bytes(c->dtype);
+    const size_t snap_bytes = 2ull * c->ny * c->nx * ab;
     const size_t total = pop_bytes + snap_bytes + sizeof(DevState);
     char* host = (char*)malloc(total);
     if (!host) {
@@ -783,7 +785,7 @@ extern "C" int lbm_load(lbm_ctx* c, const char* path) {
     for (int q = 0; q < c->probes.n; ++q) c->probes.start[q] = c->step;
     c->invalidate_graphs();
     if (!rc) rc = c->cuda(cudaMemcpy2DAsync(c->buf[c->step & 1], (size_t)c->pitch * es, host, row, row, 9ull * c->ny, cudaMemcpyHostToDevice, c->stream), "population upload");
-    if (!rc) rc = c->cuda(cudaMemcpy2DAsync(c->snap, (size_t)c->pitch * sizeof(double), host + pop_bytes, c->nx * sizeof(double), c->nx * sizeof(double), 2ull * c->ny, cudaMemcpyHostToDevice, c->stream), "snapshot upload");
+    if (!rc) rc = c->cuda(cudaMemcpy2DAsync(c->snap, (size_t)c->pitch * ab, host + pop_bytes, c->nx * ab, c->nx * ab, 2ull * c->ny, cudaMemcpyHostToDevice, c->stream), "snapshot upload");
     if (!rc) rc = c->cuda(cudaMemcpyAsync(c->d_state, host + pop_bytes + snap_bytes, sizeof(DevState), cudaMemcpyHostToDevice, c->stream), "state upload");
     if (!rc) {
         // refresh the host mirror of the last checkpoint so lbm_residual works right away

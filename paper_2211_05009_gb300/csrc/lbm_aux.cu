@@ -1,11 +1,15 @@
 // lbm_aux.cu -- per-run and on-demand kernels around the time step: initial state, field
-// import/export, FP64 mass reduction and the FP64 stream function with vortex-centre search.
+// import/export, mass reduction and the stream function with vortex-centre search.
 //
 //   init / set_moments   Sec. 2.2 (i): f = f^eq(rho, u) (Eq. 2)
 //   moments              Eq. 3 of the stored post-collision populations
-//   mass                 sum_x rho(x) in FP64 (two-stage, fixed order -> deterministic)
-//   stream_function      Psi with u_x = dPsi/dy, Psi(y = 0) = 0, trapezoid rule in y; the extrema
-//                        and their nodes give the vortex strengths and centres of Table 1 / 2.
+//   mass                 sum_x rho(x), FP64 across nodes (two-stage, fixed order -> deterministic)
+//   stream_function      Psi with u_x = dPsi/dy, Psi(y = 0) = 0, trapezoid rule in y, integrated in
+//                        FP64; the extrema and their nodes give the vortex strengths and centres of
+//                        Table 1 / Table 2.
+// Per-node arithmetic runs in the storage's arithmetic type C (FP32 for the FP32/16-bit storage
+// types, FP64 for FP64); FP64 is used from the first cross-node sum on.  On this GPU FP64 issue
+// rate is a small fraction of FP32's, so per-node FP64 math would dominate these kernels.
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 
@@ -18,60 +22,64 @@ long long row_pitch(int dtype, int nx) {
     return (nx + per_warp - 1) / per_warp * per_warp;
 }
 
-// Deviation equilibrium in FP64: g_j = w_j (drho + rho A_j(u)) (Eq. 2).
-__device__ __forceinline__ double geq_d(int j, double drho, double rho, double ux, double uy) {
-    const double cu = cx(j) * ux + cy(j) * uy;
-    const double A = 3.0 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uy * uy);
-    return wd(j) * (drho + rho * A);
+// Deviation equilibrium g_j = w_j (drho + rho A_j(u)) (Eq. 2), in the arithmetic type.
+template <typename C>
+__device__ __forceinline__ C geq_c(int j, C drho, C ux, C uy) {
+    const C cu = C(cx(j)) * ux + C(cy(j)) * uy;
+    const C A = cu * (C(3.0) + C(4.5) * cu) - C(1.5) * (ux * ux + uy * uy);
+    return C(wd(j)) * (drho + (C(1.0) + drho) * A);
 }
 
 template <typename S, bool SHIFTED>
-__device__ __forceinline__ void store_dev(S* f, long long idx, int j, double g) {
-    f[idx] = St<S>::from(typename St<S>::C(SHIFTED ? g : g + wd(j)));
+__device__ __forceinline__ typename St<S>::C load_g(const S* f, long long idx, int j) {
+    using C = typename St<S>::C;
+    const C v = St<S>::to(f[idx]);
+    return SHIFTED ? v : v - C(wd(j));
 }
 
+// Moments (Eq. 3) of the stored populations at linear index k.
 template <typename S, bool SHIFTED>
-__device__ __forceinline__ double load_dev(const S* f, long long idx, int j) {
-    const double v = double(St<S>::to(f[idx]));
-    return SHIFTED ? v : v - wd(j);
-}
-
-// Moments (Eq. 3) of the stored populations at linear index k, in FP64.
-template <typename S, bool SHIFTED>
-__device__ __forceinline__ void node_moments(const S* f, long long plane, long long k, double& drho,
-                                             double& ux, double& uy) {
-    double g[9];
+__device__ __forceinline__ void node_moments(const S* f, long long plane, long long k,
+                                             typename St<S>::C& drho, typename St<S>::C& ux,
+                                             typename St<S>::C& uy) {
+    using C = typename St<S>::C;
+    C g[9];
 #pragma unroll
-    for (int j = 0; j < 9; ++j) g[j] = load_dev<S, SHIFTED>(f, j * plane + k, j);
+    for (int j = 0; j < 9; ++j) g[j] = load_g<S, SHIFTED>(f, j * plane + k, j);
     drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
-    const double rho = 1.0 + drho;
+    const C rho = C(1.0) + drho;
     ux = ((g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7])) / rho;
     uy = ((g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8])) / rho;
 }
 
 // ------------------------------------------------------------------ init / set_moments
 template <typename S, bool SHIFTED>
-__global__ void k_init(FieldArgs a, double* snap, const double* rho_in, const double* ux_in,
+__global__ void k_init(FieldArgs a, void* snap_v, const double* rho_in, const double* ux_in,
                        const double* uy_in) {
+    using C = typename St<S>::C;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= a.pitch || y >= a.ny) return;
     S* f = static_cast<S*>(a.f);
     const long long k = (long long)y * a.pitch + x;
-    double drho = 0.0, ux = 0.0, uy = 0.0;
+    C drho = C(0), ux = C(0), uy = C(0);
     if (x < a.nx) {
         if (rho_in) {
             const long long d = (long long)y * a.nx + x;
-            drho = rho_in[d] - 1.0;
-            ux = ux_in[d];
-            uy = uy_in[d];
+            drho = C(rho_in[d] - 1.0);
+            ux = C(ux_in[d]);
+            uy = C(uy_in[d]);
         } else if (y == a.ny - 1 && (a.corner_moving || (x > 0 && x < a.nx - 1))) {
-            ux = a.U;  // Sec. 2.2 (i): only the lid moves at t = 0
+            ux = C(a.U);  // Sec. 2.2 (i): only the lid moves at t = 0
         }
     }
 #pragma unroll
-    for (int j = 0; j < 9; ++j) store_dev<S, SHIFTED>(f, j * a.plane + k, j, geq_d(j, drho, 1.0 + drho, ux, uy));
-    if (snap) {
+    for (int j = 0; j < 9; ++j) {
+        const C g = geq_c<C>(j, drho, ux, uy);
+        f[j * a.plane + k] = St<S>::from(SHIFTED ? g : g + C(wd(j)));
+    }
+    if (snap_v) {
+        C* snap = static_cast<C*>(snap_v);
         snap[k] = ux;
         snap[a.plane + k] = uy;
     }
@@ -80,16 +88,17 @@ __global__ void k_init(FieldArgs a, double* snap, const double* rho_in, const do
 // ------------------------------------------------------------------ export / import
 template <typename S, bool SHIFTED>
 __global__ void k_moments(FieldArgs a, double* rho, double* ux, double* uy) {
+    using C = typename St<S>::C;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= a.nx) return;
     const S* f = static_cast<const S*>(a.f);
-    double drho, u, v;
+    C drho, u, v;
     node_moments<S, SHIFTED>(f, a.plane, (long long)y * a.pitch + x, drho, u, v);
     const long long d = (long long)y * a.nx + x;
-    if (rho) rho[d] = 1.0 + drho;
-    if (ux) ux[d] = u;
-    if (uy) uy[d] = v;
+    if (rho) rho[d] = 1.0 + double(drho);
+    if (ux) ux[d] = double(u);
+    if (uy) uy[d] = double(v);
 }
 
 template <typename S, bool SHIFTED>
@@ -98,30 +107,35 @@ __global__ void k_get_pop(FieldArgs a, double* out) {
     const int y = blockIdx.y, j = blockIdx.z;
     if (x >= a.nx) return;
     const S* f = static_cast<const S*>(a.f);
-    out[((long long)j * a.ny + y) * a.nx + x] = load_dev<S, SHIFTED>(f, j * a.plane + (long long)y * a.pitch + x, j) + wd(j);
+    const double v = double(St<S>::to(f[j * a.plane + (long long)y * a.pitch + x]));
+    out[((long long)j * a.ny + y) * a.nx + x] = SHIFTED ? v + wd(j) : v;
 }
 
 template <typename S, bool SHIFTED>
 __global__ void k_set_pop(FieldArgs a, const double* in) {
+    using C = typename St<S>::C;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, j = blockIdx.z;
     if (x >= a.nx) return;
     S* f = static_cast<S*>(a.f);
-    store_dev<S, SHIFTED>(f, j * a.plane + (long long)y * a.pitch + x, j,
-                          in[((long long)j * a.ny + y) * a.nx + x] - wd(j));
+    const double v = in[((long long)j * a.ny + y) * a.nx + x];
+    f[j * a.plane + (long long)y * a.pitch + x] = St<S>::from(C(SHIFTED ? v - wd(j) : v));
 }
 
 // ------------------------------------------------------------------ mass
 template <typename S, bool SHIFTED>
 __global__ void __launch_bounds__(256) k_mass(FieldArgs a, double* partials) {
+    using C = typename St<S>::C;
     __shared__ double sh[8];
     const S* f = static_cast<const S*>(a.f);
     double acc = 0.0;
     for (int y = blockIdx.x; y < a.ny; y += gridDim.x)
         for (int x = threadIdx.x; x < a.nx; x += blockDim.x) {
             const long long k = (long long)y * a.pitch + x;
+            C g[9];
 #pragma unroll
-            for (int j = 0; j < 9; ++j) acc += load_dev<S, SHIFTED>(f, j * a.plane + k, j);
+            for (int j = 0; j < 9; ++j) g[j] = load_g<S, SHIFTED>(f, j * a.plane + k, j);
+            acc += double(((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8]);
         }
     acc = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
@@ -147,117 +161,139 @@ __global__ void k_mass_finalize(const double* partials, int n, double nodes, Dev
 }
 
 // ------------------------------------------------------------------ stream function
-// Block (32 columns) x (32 chunks of rows).  Psi(x, y) = sum_{k<=y} u(k) - u(0)/2 - u(y)/2,
-// which is the trapezoid sum of (u(k-1) + u(k))/2 for k = 1..y.
-constexpr int kPsiCols = 32, kPsiChunks = 32;
+// Psi(x, y) = sum_{k<=y} u(k) - u(0)/2 - u(y)/2, the trapezoid sum of (u(k-1) + u(k))/2 for
+// k = 1..y.  Three passes over (128-column) x (32-row segment) blocks:
+//   1. u_x of every node into a scratch field and the FP64 sum of each column segment;
+//   2. each segment adds the sums of the segments below it, walks its rows in FP64, writes Psi
+//      (optional) and reduces the window extrema of its block;
+//   3. one block merges the block extrema in a fixed order (ties -> smaller row-major index).
+constexpr int kPsiCols = 128, kPsiSeg = 32;
 
 struct Ext {
     double vmin, vmax;
-    long long imin, imax;  // linear node index y*nx + x (ties -> smaller index)
+    long long imin, imax;  // linear node index y*nx + x, -1 if none
 };
 
 __device__ __forceinline__ void ext_merge(Ext& a, const Ext& b) {
-    if (b.vmin < a.vmin || (b.vmin == a.vmin && b.imin < a.imin)) { a.vmin = b.vmin; a.imin = b.imin; }
-    if (b.vmax > a.vmax || (b.vmax == a.vmax && b.imax < a.imax)) { a.vmax = b.vmax; a.imax = b.imax; }
+    if (b.imin >= 0 && (a.imin < 0 || b.vmin < a.vmin || (b.vmin == a.vmin && b.imin < a.imin))) {
+        a.vmin = b.vmin;
+        a.imin = b.imin;
+    }
+    if (b.imax >= 0 && (a.imax < 0 || b.vmax > a.vmax || (b.vmax == a.vmax && b.imax < a.imax))) {
+        a.vmax = b.vmax;
+        a.imax = b.imax;
+    }
 }
 
 template <typename S, bool SHIFTED>
-__device__ __forceinline__ double node_ux(const S* f, const FieldArgs& a, int x, int y) {
-    double drho, u, v;
-    node_moments<S, SHIFTED>(f, a.plane, (long long)y * a.pitch + x, drho, u, v);
-    return u;
-}
-
-template <typename S, bool SHIFTED>
-__global__ void __launch_bounds__(kPsiCols * kPsiChunks) k_psi(FieldArgs a, double* psi, int i0, int i1, int j0,
-                                                              int j1, double* part) {
-    __shared__ double csum[kPsiChunks][kPsiCols + 1];
-    __shared__ Ext ex[kPsiChunks * kPsiCols];
+__global__ void __launch_bounds__(kPsiCols) k_psi_seg(FieldArgs a, void* uscr_v, double* segsum) {
+    using C = typename St<S>::C;
+    const int x = blockIdx.x * kPsiCols + threadIdx.x;
+    const int seg = blockIdx.y;
+    if (x >= a.nx) return;
     const S* f = static_cast<const S*>(a.f);
-    const int tx = threadIdx.x, c = threadIdx.y;
-    const int x = blockIdx.x * kPsiCols + tx;
-    const int ch = (a.ny + kPsiChunks - 1) / kPsiChunks;
-    const int y0 = c * ch, y1 = min(a.ny, y0 + ch);
+    C* uscr = static_cast<C*>(uscr_v);
+    const int y0 = seg * kPsiSeg, y1 = min(a.ny, y0 + kPsiSeg);
     double s = 0.0;
-    if (x < a.nx)
-        for (int y = y0; y < y1; ++y) s += node_ux<S, SHIFTED>(f, a, x, y);
-    csum[c][tx] = s;
-    __syncthreads();
+    for (int y = y0; y < y1; ++y) {
+        C drho, u, v;
+        node_moments<S, SHIFTED>(f, a.plane, (long long)y * a.pitch + x, drho, u, v);
+        uscr[(long long)y * a.nx + x] = u;
+        s += double(u);
+    }
+    segsum[(long long)seg * a.nx + x] = s;
+}
+
+template <typename C>
+__global__ void __launch_bounds__(kPsiCols) k_psi_walk(int nx, int ny, const C* __restrict__ uscr,
+                                                      const double* __restrict__ segsum, double* psi,
+                                                      int i0, int i1, int j0, int j1, double* part) {
+    __shared__ Ext ex[kPsiCols];
+    const int x = blockIdx.x * kPsiCols + threadIdx.x;
+    const int seg = blockIdx.y;
     Ext e{INFINITY, -INFINITY, -1, -1};
-    if (x < a.nx) {
+    if (x < nx) {
         double run = 0.0;
-        for (int k = 0; k < c; ++k) run += csum[k][tx];
-        const double u0 = node_ux<S, SHIFTED>(f, a, x, 0);
+        for (int k = 0; k < seg; ++k) run += segsum[(long long)k * nx + x];
+        const double u0 = double(uscr[x]);
         const bool colin = x >= i0 && x < i1;
+        const int y0 = seg * kPsiSeg, y1 = min(ny, y0 + kPsiSeg);
         for (int y = y0; y < y1; ++y) {
-            const double u = node_ux<S, SHIFTED>(f, a, x, y);
+            const double u = double(uscr[(long long)y * nx + x]);
             run += u;
             const double p = y == 0 ? 0.0 : run - 0.5 * u0 - 0.5 * u;
-            if (psi) psi[(long long)y * a.nx + x] = p;
+            if (psi) psi[(long long)y * nx + x] = p;
             if (colin && y >= j0 && y < j1) {
-                const long long id = (long long)y * a.nx + x;
-                if (p < e.vmin) { e.vmin = p; e.imin = id; }
-                if (p > e.vmax) { e.vmax = p; e.imax = id; }
+                const long long id = (long long)y * nx + x;
+                if (e.imin < 0 || p < e.vmin) { e.vmin = p; e.imin = id; }
+                if (e.imax < 0 || p > e.vmax) { e.vmax = p; e.imax = id; }
             }
         }
     }
-    const int t = c * kPsiCols + tx;
-    ex[t] = e;
+    ex[threadIdx.x] = e;
     __syncthreads();
-    for (int o = kPsiCols * kPsiChunks / 2; o > 0; o >>= 1) {
-        if (t < o) ext_merge(ex[t], ex[t + o]);
+    for (int o = kPsiCols / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) ext_merge(ex[threadIdx.x], ex[threadIdx.x + o]);
         __syncthreads();
     }
-    if (t == 0) {
-        part[4ll * blockIdx.x + 0] = ex[0].vmin;
-        part[4ll * blockIdx.x + 1] = (double)ex[0].imin;
-        part[4ll * blockIdx.x + 2] = ex[0].vmax;
-        part[4ll * blockIdx.x + 3] = (double)ex[0].imax;
+    if (threadIdx.x == 0) {
+        const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+        part[4 * b + 0] = ex[0].vmin;
+        part[4 * b + 1] = (double)ex[0].imin;
+        part[4 * b + 2] = ex[0].vmax;
+        part[4 * b + 3] = (double)ex[0].imax;
     }
 }
 
 __global__ void k_psi_finalize(const double* part, int nblocks, int nx, DevState* st) {
-    if (threadIdx.x != 0) return;
+    __shared__ Ext ex[256];
     Ext e{INFINITY, -INFINITY, -1, -1};
-    for (int b = 0; b < nblocks; ++b) {
-        Ext o{part[4ll * b], part[4ll * b + 2], (long long)part[4ll * b + 1], (long long)part[4ll * b + 3]};
-        if (o.imin < 0) o.vmin = INFINITY;
-        if (o.imax < 0) o.vmax = -INFINITY;
-        if (o.imin >= 0 && (e.imin < 0 || o.vmin < e.vmin || (o.vmin == e.vmin && o.imin < e.imin))) { e.vmin = o.vmin; e.imin = o.imin; }
-        if (o.imax >= 0 && (e.imax < 0 || o.vmax > e.vmax || (o.vmax == e.vmax && o.imax < e.imax))) { e.vmax = o.vmax; e.imax = o.imax; }
+    for (int b = threadIdx.x; b < nblocks; b += 256) {
+        const Ext o{part[4ll * b], part[4ll * b + 2], (long long)part[4ll * b + 1], (long long)part[4ll * b + 3]};
+        ext_merge(e, o);
     }
-    st->ext[0] = e.vmin;
-    st->ext[1] = e.imin < 0 ? -1.0 : (double)(e.imin % nx);
-    st->ext[2] = e.imin < 0 ? -1.0 : (double)(e.imin / nx);
-    st->ext[3] = e.vmax;
-    st->ext[4] = e.imax < 0 ? -1.0 : (double)(e.imax % nx);
-    st->ext[5] = e.imax < 0 ? -1.0 : (double)(e.imax / nx);
+    ex[threadIdx.x] = e;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) ext_merge(ex[threadIdx.x], ex[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        e = ex[0];
+        st->ext[0] = e.vmin;
+        st->ext[1] = e.imin < 0 ? -1.0 : (double)(e.imin % nx);
+        st->ext[2] = e.imin < 0 ? -1.0 : (double)(e.imin / nx);
+        st->ext[3] = e.vmax;
+        st->ext[4] = e.imax < 0 ? -1.0 : (double)(e.imax % nx);
+        st->ext[5] = e.imax < 0 ? -1.0 : (double)(e.imax / nx);
+    }
 }
 
 size_t psi_scratch_doubles(int nx, int ny) {
-    (void)ny;
-    return 4ull * ((nx + kPsiCols - 1) / kPsiCols);
+    const size_t nseg = (ny + kPsiSeg - 1) / kPsiSeg;
+    const size_t ncb = (nx + kPsiCols - 1) / kPsiCols;
+    return (size_t)nx * ny + nseg * nx + 4 * nseg * ncb;
 }
 
 // ------------------------------------------------------------------ dispatch
-#define LBM_DISPATCH(dtype, CALL)                                   \
-    switch (dtype) {                                                \
-        case 0: { using S = double; constexpr bool SH = false; CALL; } break;          \
-        case 1: { using S = float; constexpr bool SH = false; CALL; } break;           \
-        case 2: { using S = float; constexpr bool SH = true; CALL; } break;            \
-        case 3: { using S = __half; constexpr bool SH = true; CALL; } break;           \
-        case 4: { using S = __nv_bfloat16; constexpr bool SH = true; CALL; } break;    \
-        default: return cudaErrorInvalidValue;                      \
+#define LBM_DISPATCH(dtype, CALL)                                                      \
+    switch (dtype) {                                                                   \
+        case 0: { using S = double; constexpr bool SH = true; CALL; } break;          \
+        case 1: { using S = float; constexpr bool SH = false; CALL; } break;          \
+        case 2: { using S = float; constexpr bool SH = true; CALL; } break;           \
+        case 3: { using S = __half; constexpr bool SH = true; CALL; } break;          \
+        case 4: { using S = __nv_bfloat16; constexpr bool SH = true; CALL; } break;   \
+        default: return cudaErrorInvalidValue;                                         \
     }
 
-cudaError_t launch_init(int dtype, const FieldArgs& a, double* snap, cudaStream_t st) {
+cudaError_t launch_init(int dtype, const FieldArgs& a, void* snap, cudaStream_t st) {
     dim3 grid((unsigned)((a.pitch + 127) / 128), a.ny);
     LBM_DISPATCH(dtype, (k_init<S, SH><<<grid, 128, 0, st>>>(a, snap, nullptr, nullptr, nullptr)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_set_moments(int dtype, const FieldArgs& a, const double* rho, const double* ux,
-                               const double* uy, double* snap, cudaStream_t st) {
+                               const double* uy, void* snap, cudaStream_t st) {
     dim3 grid((unsigned)((a.pitch + 127) / 128), a.ny);
     LBM_DISPATCH(dtype, (k_init<S, SH><<<grid, 128, 0, st>>>(a, snap, rho, ux, uy)));
     return cudaGetLastError();
@@ -295,12 +331,21 @@ cudaError_t launch_mass(int dtype, const FieldArgs& a, double* partials, int max
 cudaError_t launch_stream_function(int dtype, const FieldArgs& a, double* psi, int i0, int i1,
                                    int j0, int j1, double* scratch, DevState* state,
                                    cudaStream_t st) {
-    const int nb = (a.nx + kPsiCols - 1) / kPsiCols;
-    dim3 block(kPsiCols, kPsiChunks);
-    LBM_DISPATCH(dtype, (k_psi<S, SH><<<nb, block, 0, st>>>(a, psi, i0, i1, j0, j1, scratch)));
+    const int ncb = (a.nx + kPsiCols - 1) / kPsiCols;
+    const int nseg = (a.ny + kPsiSeg - 1) / kPsiSeg;
+    double* uscr = scratch;                            // nx*ny values of the arithmetic type
+    double* segsum = scratch + (size_t)a.nx * a.ny;    // nseg * nx
+    double* part = segsum + (size_t)nseg * a.nx;       // 4 per walk block
+    dim3 grid(ncb, nseg);
+    LBM_DISPATCH(dtype, (k_psi_seg<S, SH><<<grid, kPsiCols, 0, st>>>(a, uscr, segsum)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_psi_finalize<<<1, 32, 0, st>>>(scratch, nb, a.nx, state);
+    LBM_DISPATCH(dtype, (k_psi_walk<typename St<S>::C><<<grid, kPsiCols, 0, st>>>(
+                             a.nx, a.ny, reinterpret_cast<const typename St<S>::C*>(uscr), segsum, psi,
+                             i0, i1, j0, j1, part)));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_psi_finalize<<<1, 256, 0, st>>>(part, ncb * nseg, a.nx, state);
     return cudaGetLastError();
 }
 

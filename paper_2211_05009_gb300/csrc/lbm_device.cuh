@@ -102,7 +102,7 @@ struct StepArgs {
     int s;            // steps since the last checkpoint (0..99) of the state being advanced
     DevState* state;
     ProbeSet probes;
-    double* snap;      // [2][ny][pitch] Eq. 6 snapshot (REDUCE only)
+    void* snap;        // [2][ny][pitch] Eq. 6 velocity snapshot, arithmetic type (REDUCE only)
     double* partials;  // [blocks][3]               (REDUCE only)
 };
 

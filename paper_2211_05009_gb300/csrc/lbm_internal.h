@@ -19,6 +19,9 @@ constexpr int kDefaultStepConfig = 0;
 // Geometry of the step launch for a shape (also the number of reduction partials).
 StepGeometry step_geometry(int dtype, int cfg, int ny, long long pitch);
 
+// Bytes of the arithmetic type (FP64 for FP64 storage, FP32 otherwise): the Eq. 6 snapshot type.
+inline int arith_bytes(int dtype) { return dtype == 0 ? 8 : 4; }
+
 // Row pitch (elements) for a storage type: a multiple of 32 lanes x 16 bytes.
 long long row_pitch(int dtype, int nx);
 int storage_bytes(int dtype);
@@ -36,10 +39,10 @@ struct FieldArgs {
 };
 
 // f = f^eq(1, u0) with the Sec. 2.2 (i) initial velocity; snapshot = u0.
-cudaError_t launch_init(int dtype, const FieldArgs& a, double* snap, cudaStream_t st);
+cudaError_t launch_init(int dtype, const FieldArgs& a, void* snap, cudaStream_t st);
 // f = f^eq(rho, u) from dense [ny][nx] FP64 fields; snapshot = u.
 cudaError_t launch_set_moments(int dtype, const FieldArgs& a, const double* rho, const double* ux,
-                               const double* uy, double* snap, cudaStream_t st);
+                               const double* uy, void* snap, cudaStream_t st);
 // Dense [ny][nx] FP64 moments (any output may be null).
 cudaError_t launch_moments(int dtype, const FieldArgs& a, double* rho, double* ux, double* uy,
                            cudaStream_t st);

@@ -4,7 +4,7 @@
 namespace lbm {
 
 cudaError_t launch_step_f64(int cfg, const StepArgs& a, bool reduce, cudaStream_t st) {
-    return launch_step_cfg<double, false>(cfg, a, reduce, st);
+    return launch_step_cfg<double, true>(cfg, a, reduce, st);
 }
 
 }  // namespace lbm
