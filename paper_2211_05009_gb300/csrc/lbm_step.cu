@@ -13,19 +13,17 @@ cudaError_t launch_step_bf16s(int cfg, const StepArgs& a, bool reduce, cudaStrea
 
 namespace {
 struct Shape {
-    int V, R, BY;
+    int R, BY;
 };
-// must match launch_step_cfg in lbm_step_kernel.cuh (per storage width: 8, 4, 2 bytes)
-constexpr Shape kShapes8[kStepConfigs] = {{2, 1, 4}, {2, 2, 2}, {2, 1, 8}, {2, 2, 4}, {2, 1, 2}, {2, 1, 4}};
-constexpr Shape kShapes4[kStepConfigs] = {{4, 2, 2}, {4, 1, 4}, {4, 2, 4}, {4, 1, 8}, {2, 2, 4}, {4, 2, 1}};
-constexpr Shape kShapes2[kStepConfigs] = {{4, 2, 2}, {8, 1, 4}, {4, 2, 4}, {4, 1, 4}, {2, 2, 4}, {8, 2, 2}};
+// must match launch_step_cfg in lbm_step_kernel.cuh
+constexpr Shape kShapes[kStepConfigs] = {{2, 2}, {1, 4}, {2, 2}, {4, 1}, {2, 4}, {4, 2}};
 }  // namespace
 
 StepGeometry step_geometry(int dtype, int cfg, int ny, long long pitch) {
     StepGeometry g{};
-    const int b = storage_bytes(dtype);
-    const Shape s = b == 8 ? kShapes8[cfg] : (b == 4 ? kShapes4[cfg] : kShapes2[cfg]);
-    g.grid_x = (int)(pitch / (32 * s.V));
+    const int V = storage_bytes(dtype) == 8 ? 2 : 4;
+    const Shape s = kShapes[cfg];
+    g.grid_x = (int)(pitch / (32 * V));
     g.grid_y = (ny + s.BY * s.R - 1) / (s.BY * s.R);
     g.blocks = g.grid_x * g.grid_y;
     return g;

@@ -14,10 +14,10 @@
 // the new snapshot: per node in the arithmetic type, per thread over its few nodes, and in FP64
 // from the warp level up (FP64 throughput on this part is a small fraction of FP32's).
 //
-// Thread mapping: blockDim = (32, BY); each lane owns V consecutive nodes of R consecutive rows,
-// a warp 32*V nodes per row.  All R rows are pulled before any is collided, so a thread has
-// 9*R vector loads in flight.  The row pitch is a multiple of 32*V for every launch shape, so all
-// vector accesses are in bounds; padding nodes (x >= nx) store the rest state.
+// Thread mapping: blockDim = (32, BY); each lane owns V consecutive nodes (one 16-byte vector for
+// FP32/FP64, 8 bytes for 16-bit storage) of R consecutive rows, a warp 32*V nodes per row.  The
+// row pitch is a multiple of 32*V for every launch shape, so all vector accesses are in bounds;
+// padding nodes (x >= nx) store the rest state.
 #pragma once
 
 #include "lbm_device.cuh"
@@ -32,13 +32,63 @@ template <> struct Raw<16> { using T = uint4; };
 template <> struct Raw<8> { using T = uint2; };
 template <> struct Raw<4> { using T = unsigned int; };
 
-template <typename S, int V>
+// Read-only vector load; HINT = 1 adds an L2 256-byte prefetch and skips L1 allocation.
+template <typename T, int HINT>
+__device__ __forceinline__ T ldg_vec(const T* p) {
+    if constexpr (HINT == 0) {
+        return __ldg(p);
+    } else if constexpr (sizeof(T) == 16) {
+        uint4 r;
+        asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+        return r;
+    } else if constexpr (sizeof(T) == 8) {
+        uint2 r;
+        asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v2.u32 {%0, %1}, [%2];"
+                     : "=r"(r.x), "=r"(r.y) : "l"(p));
+        return r;
+    } else {
+        unsigned int r;
+        asm volatile("ld.global.nc.L1::no_allocate.L2::256B.u32 %0, [%1];" : "=r"(r) : "l"(p));
+        return r;
+    }
+}
+
+template <typename S, int V, int HINT = 0>
 __device__ __forceinline__ void vload_n(const S* __restrict__ p, typename St<S>::C (&out)[V]) {
     using T = typename Raw<V * sizeof(S)>::T;
     union { T u; S s[V]; } b;
-    b.u = __ldg(reinterpret_cast<const T*>(p));
+    b.u = ldg_vec<T, HINT>(reinterpret_cast<const T*>(p));
 #pragma unroll
     for (int i = 0; i < V; ++i) out[i] = St<S>::to(b.s[i]);
+}
+
+// V values of a plain arithmetic-type array (the Eq. 6 snapshot), in 16-byte pieces.
+template <typename C, int V>
+__device__ __forceinline__ void cload(const C* p, C (&out)[V]) {
+    constexpr int B = V * sizeof(C) < 16 ? V * sizeof(C) : 16;
+    constexpr int PER = B / sizeof(C);
+    using T = typename Raw<B>::T;
+#pragma unroll
+    for (int k = 0; k < V; k += PER) {
+        union { T u; C c[PER]; } b;
+        b.u = *reinterpret_cast<const T*>(p + k);
+#pragma unroll
+        for (int i = 0; i < PER; ++i) out[k + i] = b.c[i];
+    }
+}
+template <typename C, int V>
+__device__ __forceinline__ void cstore(C* p, const C (&in)[V]) {
+    constexpr int B = V * sizeof(C) < 16 ? V * sizeof(C) : 16;
+    constexpr int PER = B / sizeof(C);
+    using T = typename Raw<B>::T;
+#pragma unroll
+    for (int k = 0; k < V; k += PER) {
+        union { T u; C c[PER]; } b;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) b.c[i] = in[k + i];
+        *reinterpret_cast<T*>(p + k) = b.u;
+    }
 }
 
 template <typename S, int V>
@@ -51,12 +101,12 @@ __device__ __forceinline__ void vstore_n(S* __restrict__ p, const typename St<S>
 }
 
 // Pull one population row segment: out[i] = value at (x0 + i - DX), DX = c_x of the direction.
-template <typename S, bool SHIFTED, int V, int DX>
+template <typename S, bool SHIFTED, int V, int DX, int HINT>
 __device__ __forceinline__ void pull_row(const S* __restrict__ p, int lane, int x0, long long pitch,
                                          typename St<S>::C wj, typename St<S>::C (&out)[V]) {
     using C = typename St<S>::C;
     C v[V];
-    vload_n<S, V>(p, v);
+    vload_n<S, V, HINT>(p, v);
     if constexpr (DX == 0) {
 #pragma unroll
         for (int i = 0; i < V; ++i) out[i] = v[i];
@@ -104,7 +154,7 @@ template <> __device__ __forceinline__ double rcp<double>(double v) { return __d
 
 // Streamed populations of one row segment (V nodes) of row y, walls folded in: wall rows gather
 // at their inner row, the left/right wall nodes take the populations of x_f = 1 / nx - 2.
-template <typename S, bool SHIFTED, int V>
+template <typename S, bool SHIFTED, int V, int HINT>
 __device__ __forceinline__ void pull_segment(const S* __restrict__ src, int lane, int x0, int y, int nx,
                                              int ny, long long pitch, long long plane,
                                              typename St<S>::C (&f)[9][V]) {
@@ -113,15 +163,15 @@ __device__ __forceinline__ void pull_segment(const S* __restrict__ src, int lane
     const S* pc = src + (long long)yc * pitch + x0;
     const S* ps = pc - pitch;  // row yc - 1: source of c_y = +1
     const S* pn = pc + pitch;  // row yc + 1: source of c_y = -1
-    pull_row<S, SHIFTED, V, 0>(pc + 0 * plane, lane, x0, pitch, C(4.0 / 9.0), f[0]);
-    pull_row<S, SHIFTED, V, 1>(pc + 1 * plane, lane, x0, pitch, C(1.0 / 9.0), f[1]);
-    pull_row<S, SHIFTED, V, 0>(ps + 2 * plane, lane, x0, pitch, C(1.0 / 9.0), f[2]);
-    pull_row<S, SHIFTED, V, -1>(pc + 3 * plane, lane, x0, pitch, C(1.0 / 9.0), f[3]);
-    pull_row<S, SHIFTED, V, 0>(pn + 4 * plane, lane, x0, pitch, C(1.0 / 9.0), f[4]);
-    pull_row<S, SHIFTED, V, 1>(ps + 5 * plane, lane, x0, pitch, C(1.0 / 36.0), f[5]);
-    pull_row<S, SHIFTED, V, -1>(ps + 6 * plane, lane, x0, pitch, C(1.0 / 36.0), f[6]);
-    pull_row<S, SHIFTED, V, -1>(pn + 7 * plane, lane, x0, pitch, C(1.0 / 36.0), f[7]);
-    pull_row<S, SHIFTED, V, 1>(pn + 8 * plane, lane, x0, pitch, C(1.0 / 36.0), f[8]);
+    pull_row<S, SHIFTED, V, 0, HINT>(pc + 0 * plane, lane, x0, pitch, C(4.0 / 9.0), f[0]);
+    pull_row<S, SHIFTED, V, 1, HINT>(pc + 1 * plane, lane, x0, pitch, C(1.0 / 9.0), f[1]);
+    pull_row<S, SHIFTED, V, 0, HINT>(ps + 2 * plane, lane, x0, pitch, C(1.0 / 9.0), f[2]);
+    pull_row<S, SHIFTED, V, -1, HINT>(pc + 3 * plane, lane, x0, pitch, C(1.0 / 9.0), f[3]);
+    pull_row<S, SHIFTED, V, 0, HINT>(pn + 4 * plane, lane, x0, pitch, C(1.0 / 9.0), f[4]);
+    pull_row<S, SHIFTED, V, 1, HINT>(ps + 5 * plane, lane, x0, pitch, C(1.0 / 36.0), f[5]);
+    pull_row<S, SHIFTED, V, -1, HINT>(ps + 6 * plane, lane, x0, pitch, C(1.0 / 36.0), f[6]);
+    pull_row<S, SHIFTED, V, -1, HINT>(pn + 7 * plane, lane, x0, pitch, C(1.0 / 36.0), f[7]);
+    pull_row<S, SHIFTED, V, 1, HINT>(pn + 8 * plane, lane, x0, pitch, C(1.0 / 36.0), f[8]);
     if (x0 == 0) {
 #pragma unroll
         for (int j = 0; j < 9; ++j) f[j][0] = f[j][1];
@@ -143,8 +193,8 @@ __device__ __forceinline__ void pull_segment(const S* __restrict__ src, int lane
     }
 }
 
-template <typename S, bool SHIFTED, bool REDUCE, int V, int R, int BY, int MINB>
-__global__ void __launch_bounds__(32 * BY, MINB) k_step(const StepArgs a) {
+template <typename S, bool SHIFTED, bool REDUCE, int V, int R, int BY, int HINT>
+__global__ void __launch_bounds__(32 * BY) k_step(const StepArgs a) {
     using C = typename St<S>::C;
     const int lane = threadIdx.x;
     const int x0 = (blockIdx.x * 32 + lane) * V;
@@ -159,15 +209,18 @@ __global__ void __launch_bounds__(32 * BY, MINB) k_step(const StepArgs a) {
 
     C acc_drho = C(0), acc_num = C(0), acc_den = C(0);
 
-    // all R rows are loaded first (rows past the top are clamped for loading and not stored)
-    C f[R][9][V];
-#pragma unroll
-    for (int r = 0; r < R; ++r) pull_segment<S, SHIFTED, V>(src, lane, x0, min(yb + r, ny - 1), nx, ny, pitch, plane, f[r]);
-
-#pragma unroll
+#pragma unroll 1
     for (int r = 0; r < R; ++r) {
         const int y = yb + r;
         if (y >= ny) break;  // uniform across the warp
+        C f[9][V];
+        pull_segment<S, SHIFTED, V, HINT>(src, lane, x0, y, nx, ny, pitch, plane, f);
+        C* snap = static_cast<C*>(a.snap);
+        C sx[V], sy[V];
+        if constexpr (REDUCE) {
+            cload<C, V>(snap + (long long)y * pitch + x0, sx);
+            cload<C, V>(snap + plane + (long long)y * pitch + x0, sy);
+        }
         // observing points on this row segment (Sec. 3.3)
         unsigned pmask = 0;
         for (int q = 0; q < a.probes.n; ++q)
@@ -177,7 +230,7 @@ __global__ void __launch_bounds__(32 * BY, MINB) k_step(const StepArgs a) {
             const int x = x0 + i;
             C g[9];
 #pragma unroll
-            for (int j = 0; j < 9; ++j) g[j] = f[r][j][i];
+            for (int j = 0; j < 9; ++j) g[j] = f[j][i];
             const C drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
             const C rho = C(1.0) + drho;
             const C jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
@@ -195,7 +248,7 @@ __global__ void __launch_bounds__(32 * BY, MINB) k_step(const StepArgs a) {
                 C ew[9];
                 geq9<C>(drho, rho, uox, uoy, ew);
 #pragma unroll
-                for (int j = 0; j < 9; ++j) f[r][j][i] = ew[j] + keep * (g[j] - e[j]);
+                for (int j = 0; j < 9; ++j) f[j][i] = ew[j] + keep * (g[j] - e[j]);
             } else {
                 // BGK as an increment d_j = (f^eq_j - f_j)/tau added to the pulled value.  The
                 // increment must carry no momentum; in FP32 the rounding of f^eq breaks that by a
@@ -213,24 +266,21 @@ __global__ void __launch_bounds__(32 * BY, MINB) k_step(const StepArgs a) {
                     d[4] += C(0.5) * my;
                 }
 #pragma unroll
-                for (int j = 0; j < 9; ++j) f[r][j][i] = g[j] + d[j];
+                for (int j = 0; j < 9; ++j) f[j][i] = g[j] + d[j];
             }
             if (x >= nx) {
 #pragma unroll
-                for (int j = 0; j < 9; ++j) f[r][j][i] = C(0.0);
+                for (int j = 0; j < 9; ++j) f[j][i] = C(0.0);
             }
             if constexpr (REDUCE) {
                 if (x < nx) {
-                    C* snap = static_cast<C*>(a.snap);
-                    const long long k = (long long)y * pitch + x;
-                    const C sx = snap[k], sy = snap[plane + k];
-                    const C dx = uox - sx, dy = uoy - sy;  // exact when close (Sterbenz)
+                    const C dx = uox - sx[i], dy = uoy - sy[i];  // exact when close (Sterbenz)
                     acc_drho += drho;
                     acc_num += dx * dx + dy * dy;
-                    acc_den += sx * sx + sy * sy;
-                    snap[k] = uox;
-                    snap[plane + k] = uoy;
+                    acc_den += sx[i] * sx[i] + sy[i] * sy[i];
                 }
+                sx[i] = x < nx ? uox : C(0);
+                sy[i] = x < nx ? uoy : C(0);
             }
             if (pmask) {
                 for (int q = 0; q < a.probes.n; ++q) {
@@ -255,9 +305,13 @@ __global__ void __launch_bounds__(32 * BY, MINB) k_step(const StepArgs a) {
         for (int j = 0; j < 9; ++j) {
             if constexpr (!SHIFTED) {
 #pragma unroll
-                for (int i = 0; i < V; ++i) f[r][j][i] += C(wd(j));
+                for (int i = 0; i < V; ++i) f[j][i] += C(wd(j));
             }
-            vstore_n<S, V>(pd + j * plane, f[r][j]);
+            vstore_n<S, V>(pd + j * plane, f[j]);
+        }
+        if constexpr (REDUCE) {
+            cstore<C, V>(snap + (long long)y * pitch + x0, sx);
+            cstore<C, V>(snap + plane + (long long)y * pitch + x0, sy);
         }
     }
 
@@ -281,52 +335,31 @@ __global__ void __launch_bounds__(32 * BY, MINB) k_step(const StepArgs a) {
     }
 }
 
-// Launch shape (nodes per lane V, rows per thread R, warps per block BY, min blocks per SM).
-// Every shape computes bitwise-identical populations; only speed differs.
-template <typename S, bool SHIFTED, int V, int R, int BY, int MINB>
+// Launch shape (nodes per lane V, rows per thread R, warps per block BY, load hint).  Every shape
+// computes bitwise-identical populations; only speed differs.
+template <typename S, bool SHIFTED, int V, int R, int BY, int HINT>
 static cudaError_t launch_step_shape(const StepArgs& a, bool reduce, cudaStream_t st) {
     dim3 block(32, BY);
     dim3 grid((unsigned)(a.pitch / (32 * V)), (unsigned)((a.ny + BY * R - 1) / (BY * R)));
     if (reduce)
-        k_step<S, SHIFTED, true, V, R, BY, MINB><<<grid, block, 0, st>>>(a);
+        k_step<S, SHIFTED, true, V, R, BY, HINT><<<grid, block, 0, st>>>(a);
     else
-        k_step<S, SHIFTED, false, V, R, BY, MINB><<<grid, block, 0, st>>>(a);
+        k_step<S, SHIFTED, false, V, R, BY, HINT><<<grid, block, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-// The shape tables; step_shape() in lbm_step.cu mirrors them.
+// The shape tables; kShapes* in lbm_step.cu mirror them.
 template <typename S, bool SHIFTED>
 static cudaError_t launch_step_cfg(int cfg, const StepArgs& a, bool reduce, cudaStream_t st) {
-    if constexpr (sizeof(S) == 8) {
-        switch (cfg) {
-            case 0: return launch_step_shape<S, SHIFTED, 2, 1, 4, 1>(a, reduce, st);
-            case 1: return launch_step_shape<S, SHIFTED, 2, 2, 2, 1>(a, reduce, st);
-            case 2: return launch_step_shape<S, SHIFTED, 2, 1, 8, 1>(a, reduce, st);
-            case 3: return launch_step_shape<S, SHIFTED, 2, 2, 4, 1>(a, reduce, st);
-            case 4: return launch_step_shape<S, SHIFTED, 2, 1, 2, 1>(a, reduce, st);
-            case 5: return launch_step_shape<S, SHIFTED, 2, 1, 4, 4>(a, reduce, st);
-            default: return cudaErrorInvalidValue;
-        }
-    } else if constexpr (sizeof(S) == 4) {
-        switch (cfg) {
-            case 0: return launch_step_shape<S, SHIFTED, 4, 2, 2, 1>(a, reduce, st);
-            case 1: return launch_step_shape<S, SHIFTED, 4, 1, 4, 1>(a, reduce, st);
-            case 2: return launch_step_shape<S, SHIFTED, 4, 2, 4, 1>(a, reduce, st);
-            case 3: return launch_step_shape<S, SHIFTED, 4, 1, 8, 1>(a, reduce, st);
-            case 4: return launch_step_shape<S, SHIFTED, 2, 2, 4, 1>(a, reduce, st);
-            case 5: return launch_step_shape<S, SHIFTED, 4, 2, 1, 1>(a, reduce, st);
-            default: return cudaErrorInvalidValue;
-        }
-    } else {
-        switch (cfg) {
-            case 0: return launch_step_shape<S, SHIFTED, 4, 2, 2, 1>(a, reduce, st);
-            case 1: return launch_step_shape<S, SHIFTED, 8, 1, 4, 1>(a, reduce, st);
-            case 2: return launch_step_shape<S, SHIFTED, 4, 2, 4, 1>(a, reduce, st);
-            case 3: return launch_step_shape<S, SHIFTED, 4, 1, 4, 1>(a, reduce, st);
-            case 4: return launch_step_shape<S, SHIFTED, 2, 2, 4, 1>(a, reduce, st);
-            case 5: return launch_step_shape<S, SHIFTED, 8, 2, 2, 1>(a, reduce, st);
-            default: return cudaErrorInvalidValue;
-        }
+    constexpr int V = 16 / sizeof(S) < 4 ? 16 / sizeof(S) : 4;  // 2 for FP64, else 4
+    switch (cfg) {
+        case 0: return launch_step_shape<S, SHIFTED, V, 2, 2, 0>(a, reduce, st);
+        case 1: return launch_step_shape<S, SHIFTED, V, 1, 4, 0>(a, reduce, st);
+        case 2: return launch_step_shape<S, SHIFTED, V, 2, 2, 1>(a, reduce, st);
+        case 3: return launch_step_shape<S, SHIFTED, V, 4, 1, 0>(a, reduce, st);
+        case 4: return launch_step_shape<S, SHIFTED, V, 2, 4, 0>(a, reduce, st);
+        case 5: return launch_step_shape<S, SHIFTED, V, 4, 2, 1>(a, reduce, st);
+        default: return cudaErrorInvalidValue;
     }
 }
 
