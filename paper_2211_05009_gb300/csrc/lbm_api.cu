@@ -63,7 +63,7 @@ struct lbm_ctx {
     cudaEvent_t ev[2] = {nullptr, nullptr};
 
     ProbeSet probes{};
-    int cfg = kDefaultStepConfig;  // launch shape of the step kernel
+    int cfg = 0;  // launch shape of the step kernel
     StepGeometry geo{};
     std::string err;
 
@@ -287,6 +287,7 @@ extern "C" int lbm_create_ex(int nx, int ny, double tau, double U, lbm_dtype dty
     c->alloc_user = g_alloc_user;
     c->pitch = row_pitch(c->dtype, nx);
     c->plane = c->pitch * (long long)ny;
+    c->cfg = default_step_config(c->dtype);
     c->geo = step_geometry(c->dtype, c->cfg, ny, c->pitch);
     int max_blocks = 0;
     for (int k = 0; k < kStepConfigs; ++k) {

@@ -14,7 +14,12 @@ struct StepGeometry {
 
 // Launch shapes of the step kernel (see lbm_step_kernel.cuh); all give identical populations.
 constexpr int kStepConfigs = 6;
-constexpr int kDefaultStepConfig = 0;
+// Fastest shape per storage type measured on GB300 at 2048 x 2048 (f64, f32, f32s, f16s, bf16s);
+// lbm_autotune re-measures on the caller's size.
+inline int default_step_config(int dtype) {
+    constexpr int k[5] = {1, 3, 3, 2, 2};
+    return (dtype >= 0 && dtype < 5) ? k[dtype] : 0;
+}
 
 // Geometry of the step launch for a shape (also the number of reduction partials).
 StepGeometry step_geometry(int dtype, int cfg, int ny, long long pitch);

@@ -26,12 +26,18 @@ def main(argv=None):
     ap.add_argument("--dtype", default="f32s", choices=sorted(B.DTYPES))
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=0)
+    ap.add_argument("--config", type=int, default=None, help="launch shape of the step kernel")
+    ap.add_argument("--autotune", action="store_true", help="pick the fastest launch shape first")
     a = ap.parse_args(argv)
     build()
     stream = torch.cuda.current_stream()
     ctx = B.lbm_create(a.nx, a.ny, a.re, a.u, a.dtype)
     try:
         B.lbm_set_stream(ctx, stream.cuda_stream)
+        if a.config is not None:
+            B.lbm_set_launch_config(ctx, a.config)
+        if a.autotune:
+            B.lbm_autotune(ctx, 40)
         if a.warmup:
             B.lbm_step(ctx, a.warmup)
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -43,7 +49,7 @@ def main(argv=None):
         sec = t0.elapsed_time(t1) / 1e3
         out = {"nx": a.nx, "ny": a.ny, "Re": a.re, "U": a.u, "dtype": a.dtype, "steps": a.steps,
                "seconds": sec, "glups": a.nx * a.ny * a.steps / sec / 1e9 if sec > 0 else None,
-               "mass": B.lbm_mass(ctx)}
+               "mass": B.lbm_mass(ctx), "launch_config": B.lbm_get_info(ctx).launch_config}
         if a.warmup + a.steps >= B.RESIDUAL_INTERVAL:
             out["residual"] = B.lbm_residual(ctx)
         out["psi_min"], out["xc"], out["yc"] = B.lbm_stream_function(ctx)
