@@ -46,6 +46,7 @@ extern "C" {
 #define LBM_ETIMEOUT 5  /* a bounded device-side wait ran out                                    */
 #define LBM_ENOTREADY 6 /* the value does not exist yet (no residual before the first 100 steps) */
 #define LBM_EIO 7       /* checkpoint file could not be written, read or did not match          */
+#define LBM_ETOOBIG 8   /* grid too large for the fixed scratch of lbm_stream_function_static   */
 
 /* Storage type of the populations.  Arithmetic is FP64 for LBM_F64 and FP32 otherwise.
  * The *S types (and LBM_F64) store the shifted deviation g_j = f_j - w_j instead of f_j. */
@@ -196,6 +197,30 @@ int lbm_probe_count(lbm_ctx *ctx, int p, long *n);
 
 /* Remove all probes. */
 int lbm_probe_clear(lbm_ctx *ctx);
+
+/* Allocation-free stream function.  The paper has no counterpart: this is a service for callers
+ * that cannot call cudaMalloc -- e.g. a solver embedded in an application that reserves its whole
+ * device-memory budget at start-up and forbids allocation afterwards.  It computes what
+ * lbm_stream_function computes (Psi = 0 on the bottom wall, u_x = dPsi/dy, trapezoid rule in y,
+ * FP64 sums), but from a caller-supplied velocity field and without a context:
+ *   ux      DEVICE [ny][nx] FP64 u_x field (e.g. from lbm_moments into device memory), read only;
+ *   psi     optional DEVICE [ny][nx] FP64 output (NULL: not written);
+ *   result  DEVICE buffer of 3 doubles: psi_min, and its node as x/nx and y/nx (width units);
+ *   stream  cudaStream_t to queue on (NULL: legacy stream).  Asynchronous; nothing is copied to
+ *           the host and no host synchronisation happens.
+ * Scratch: a fixed device array of LBM_STATIC_SCRATCH_DOUBLES doubles (4 MiB), defined in the
+ * library and held by every GPU that loads it until the process exits.  A call needs
+ * nx*ceil(ny/32) + 2*ceil(ny/32)*ceil(nx/128) doubles of it (a 4096 x 4000 grid fits); larger
+ * grids return LBM_ETOOBIG without launching anything.  Every element a call reads it has
+ * written first, so nothing needs to be cleared between calls; but all calls share the one
+ * array, so calls that can overlap on the GPU (other streams, other host threads) race and
+ * must be ordered by the caller.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture.  Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ * Errors: LBM_EINVAL (NULL ux/result, nx or ny < 1), LBM_ETOOBIG, LBM_ECUDA. */
+#define LBM_STATIC_SCRATCH_DOUBLES (1 << 19)
+int lbm_stream_function_static(const double *ux, int nx, int ny, double *psi, double *result,
+                               void *stream);
 
 /* ------------------------------------------------------------------ checkpoint */
 

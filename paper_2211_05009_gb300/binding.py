@@ -16,9 +16,10 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "liblbm.so")
 
-LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EDIVERGED, LBM_ETIMEOUT, LBM_ENOTREADY, LBM_EIO = range(8)
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EDIVERGED, LBM_ETIMEOUT, LBM_ENOTREADY, LBM_EIO, LBM_ETOOBIG = range(9)
 ERROR_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_EDIVERGED",
-               5: "LBM_ETIMEOUT", 6: "LBM_ENOTREADY", 7: "LBM_EIO"}
+               5: "LBM_ETIMEOUT", 6: "LBM_ENOTREADY", 7: "LBM_EIO", 8: "LBM_ETOOBIG"}
+LBM_STATIC_SCRATCH_DOUBLES = 1 << 19
 DTYPES = {"f64": 0, "f32": 1, "f32s": 2, "f16s": 3, "bf16s": 4}
 LBM_FLAG_LID_CORNERS_MOVING = 1
 LBM_MAX_PROBES = 4
@@ -70,6 +71,7 @@ _SIGS = [
     ("lbm_probe", _I, [_P, _D, _D, _I, _P, _L]),
     ("lbm_probe_count", _I, [_P, _I, ctypes.POINTER(_L)]),
     ("lbm_probe_clear", _I, [_P]),
+    ("lbm_stream_function_static", _I, [_P, _I, _I, _P, _P, _P]),
     ("lbm_save", _I, [_P, ctypes.c_char_p]),
     ("lbm_load", _I, [_P, ctypes.c_char_p]),
 ]
@@ -240,6 +242,13 @@ def lbm_probe_count(ctx, p: int) -> int:
 
 def lbm_probe_clear(ctx) -> None:
     _check(ctx, library().lbm_probe_clear(ctx))
+
+
+def lbm_stream_function_static(ux, nx: int, ny: int, psi, result, stream_handle=None) -> int:
+    """Allocation-free stream function of a device u_x field (no context).  ux, psi and result are
+    device buffers; returns the library's code (LBM_OK, LBM_EINVAL, LBM_ETOOBIG, LBM_ECUDA)."""
+    return library().lbm_stream_function_static(_ptr(ux), int(nx), int(ny), _ptr(psi), _ptr(result),
+                                                 stream_handle)
 
 
 def lbm_save(ctx, path: str) -> None:
