@@ -163,7 +163,7 @@ def read_profile_traffic():
         if ":" in ln:
             k, v = ln.split(":", 1)
             vals[k.strip()] = v.strip()
-    src = os.path.join(ROOT, "paper_2211_05009_gb300", "csrc", "lbm_step.cu")
+    src = os.path.join(ROOT, "paper_2211_05009_gb300", "csrc", "lbm_step_kernel.cuh")
     digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     if vals.get("kernel_source_sha256_16") != digest:
         return None
