@@ -222,6 +222,64 @@ int lbm_probe_clear(lbm_ctx *ctx);
 int lbm_stream_function_static(const double *ux, int nx, int ny, double *psi, double *result,
                                void *stream);
 
+/* ------------------------------------------------------------------ batched sweep */
+
+/* A set of independent cavities of uneven sizes stepped together in one persistent GPU launch per
+ * 100-step interval (the Re x Ar survey of Sec. 3.3, Fig. 17).  Cavity i has nx[i] x ny[i] nodes,
+ * Reynolds number Re[i] and lid speed U[i] (tau_i from Re = U nx / nu and Eq. 5, as lbm_create);
+ * all share one storage type.  Every cavity starts from the Sec. 2.2 (i) state.  At each
+ * checkpoint every active cavity gets its own Eq. 6 residual and mass; lbm_batch_run_to_residual
+ * retires cavities whose residual fell below tol and compacts the work list, so converged
+ * cavities cost nothing afterwards.  The launch is cooperative; every grid-barrier wait inside it
+ * is bounded (default 2 s) and a wait that runs out makes the call return LBM_ETIMEOUT.
+ * Device memory comes from cudaMalloc (the allocator hook applies to single cavities only). */
+#define LBM_BATCH_MAX 512
+typedef struct lbm_batch lbm_batch;
+
+/* Errors: LBM_EINVAL (n outside 1..LBM_BATCH_MAX, a grid < 3, tau <= 1/2), LBM_ENOMEM, LBM_ECUDA;
+ * on failure *out is NULL and lbm_batch_last_error(NULL) holds the reason. */
+int lbm_batch_create(int n, const int *nx, const int *ny, const double *Re, const double *U,
+                     lbm_dtype dtype, lbm_batch **out);
+void lbm_batch_destroy(lbm_batch *b);
+const char *lbm_batch_last_error(const lbm_batch *b);
+int lbm_batch_set_stream(lbm_batch *b, void *cuda_stream);
+
+/* Advance every active cavity n >= 0 steps (no retirement).  Synchronising. */
+int lbm_batch_step(lbm_batch *b, long n);
+
+/* Run until every cavity's Eq. 6 residual is below tol (> 0) or max_steps more steps were taken;
+ * steps_done[n] (host, may be NULL) receives each cavity's steps in this call.  LBM_OK when all
+ * converged, LBM_ENOTREADY otherwise, LBM_EDIVERGED if a cavity went non-finite. */
+int lbm_batch_run_to_residual(lbm_batch *b, double tol, long max_steps, long *steps_done);
+
+/* Latest per-cavity Eq. 6 residuals (host r[n]) and states (host status[n] or NULL: 0 active,
+ * 1 converged, 2 stopped at the step cap, 3 non-finite). */
+int lbm_batch_residual(lbm_batch *b, double *r, int *status);
+
+/* Global step of each cavity's current state (host steps[n]). */
+int lbm_batch_cavity_steps(lbm_batch *b, long *steps);
+
+/* Cavity i's moments / populations / stream function, as the single-cavity calls, into DEVICE
+ * buffers sized for that cavity.  Synchronising. */
+int lbm_batch_moments(lbm_batch *b, int i, double *rho, double *ux, double *uy);
+int lbm_batch_get_populations(lbm_batch *b, int i, double *f);
+int lbm_batch_stream_function(lbm_batch *b, int i, double *psi, double *psi_min, double *xc,
+                              double *yc);
+
+/* One observing point per cavity at (x[i], y[i]) (width units, as lbm_probe); after every step
+ * t with t % every == 0 cavity i writes (u_x, u_y) to dev_series[2 (i cap + k)], k = sample
+ * number mod cap.  dev_series: caller-owned DEVICE buffer of 2 n cap doubles. */
+int lbm_batch_probe(lbm_batch *b, const double *x, const double *y, int every, double *dev_series,
+                    long cap);
+
+/* Cavity i's parameters (launch_config holds the persistent grid's block count). */
+int lbm_batch_info(lbm_batch *b, int i, lbm_info *info);
+
+/* Limit of each grid-barrier wait in seconds (default 2).  absent_block >= 0 makes that block of
+ * the next launch leave before its first barrier -- a fault-injection hook for testing the
+ * timeout path (the other blocks' waits run out and the call returns LBM_ETIMEOUT). */
+int lbm_batch_set_barrier_limit(lbm_batch *b, double seconds, int absent_block);
+
 /* ------------------------------------------------------------------ checkpoint */
 
 /* Write / read the complete state (header with nx, ny, dtype, tau, U, flags, step; the stored

@@ -72,6 +72,20 @@ _SIGS = [
     ("lbm_probe_count", _I, [_P, _I, ctypes.POINTER(_L)]),
     ("lbm_probe_clear", _I, [_P]),
     ("lbm_stream_function_static", _I, [_P, _I, _I, _P, _P, _P]),
+    ("lbm_batch_create", _I, [_I, _P, _P, _P, _P, _I, ctypes.POINTER(_P)]),
+    ("lbm_batch_destroy", None, [_P]),
+    ("lbm_batch_last_error", ctypes.c_char_p, [_P]),
+    ("lbm_batch_set_stream", _I, [_P, _P]),
+    ("lbm_batch_step", _I, [_P, _L]),
+    ("lbm_batch_run_to_residual", _I, [_P, _D, _L, _P]),
+    ("lbm_batch_residual", _I, [_P, _P, _P]),
+    ("lbm_batch_cavity_steps", _I, [_P, _P]),
+    ("lbm_batch_moments", _I, [_P, _I, _P, _P, _P]),
+    ("lbm_batch_get_populations", _I, [_P, _I, _P]),
+    ("lbm_batch_stream_function", _I, [_P, _I, _P, _DP, _DP, _DP]),
+    ("lbm_batch_probe", _I, [_P, _P, _P, _I, _P, _L]),
+    ("lbm_batch_info", _I, [_P, _I, ctypes.POINTER(lbm_info)]),
+    ("lbm_batch_set_barrier_limit", _I, [_P, _D, _I]),
     ("lbm_save", _I, [_P, ctypes.c_char_p]),
     ("lbm_load", _I, [_P, ctypes.c_char_p]),
 ]
@@ -257,3 +271,90 @@ def lbm_save(ctx, path: str) -> None:
 
 def lbm_load(ctx, path: str) -> None:
     _check(ctx, library().lbm_load(ctx, path.encode()))
+
+
+# ------------------------------------------------------------------ batched sweep
+def _bcheck(b, rc: int):
+    if rc != LBM_OK:
+        raise LBMError(rc, library().lbm_batch_last_error(b).decode(errors="replace"))
+
+
+def lbm_batch_create(nx, ny, Re, U, dtype: str | int = "f32s"):
+    n = len(nx)
+    a_nx = np.ascontiguousarray(nx, dtype=np.int32)
+    a_ny = np.ascontiguousarray(ny, dtype=np.int32)
+    a_re = np.ascontiguousarray(Re, dtype=np.float64)
+    a_u = np.ascontiguousarray(U, dtype=np.float64)
+    out = ctypes.c_void_p()
+    rc = library().lbm_batch_create(n, a_nx.ctypes.data, a_ny.ctypes.data, a_re.ctypes.data, a_u.ctypes.data,
+                                    DTYPES.get(dtype, dtype), ctypes.byref(out))
+    _bcheck(None, rc)
+    return out.value
+
+
+def lbm_batch_destroy(b) -> None:
+    library().lbm_batch_destroy(b)
+
+
+def lbm_batch_last_error(b) -> str:
+    return library().lbm_batch_last_error(b).decode(errors="replace")
+
+
+def lbm_batch_set_stream(b, stream_handle) -> None:
+    _bcheck(b, library().lbm_batch_set_stream(b, stream_handle))
+
+
+def lbm_batch_step(b, n: int) -> None:
+    _bcheck(b, library().lbm_batch_step(b, int(n)))
+
+
+def lbm_batch_run_to_residual(b, n_cav: int, tol: float, max_steps: int):
+    """(return code, steps per cavity); LBM_OK / LBM_ENOTREADY are returned, others raise."""
+    done = np.zeros(n_cav, dtype=np.int64)
+    rc = library().lbm_batch_run_to_residual(b, float(tol), int(max_steps), done.ctypes.data)
+    if rc not in (LBM_OK, LBM_ENOTREADY):
+        _bcheck(b, rc)
+    return rc, done
+
+
+def lbm_batch_residual(b, n_cav: int):
+    r = np.zeros(n_cav)
+    st = np.zeros(n_cav, dtype=np.int32)
+    _bcheck(b, library().lbm_batch_residual(b, r.ctypes.data, st.ctypes.data))
+    return r, st
+
+
+def lbm_batch_cavity_steps(b, n_cav: int):
+    s = np.zeros(n_cav, dtype=np.int64)
+    _bcheck(b, library().lbm_batch_cavity_steps(b, s.ctypes.data))
+    return s
+
+
+def lbm_batch_moments(b, i: int, rho=None, ux=None, uy=None) -> None:
+    _bcheck(b, library().lbm_batch_moments(b, i, _ptr(rho), _ptr(ux), _ptr(uy)))
+
+
+def lbm_batch_get_populations(b, i: int, f) -> None:
+    _bcheck(b, library().lbm_batch_get_populations(b, i, _ptr(f)))
+
+
+def lbm_batch_stream_function(b, i: int, psi=None):
+    vmin, xc, yc = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _bcheck(b, library().lbm_batch_stream_function(b, i, _ptr(psi), ctypes.byref(vmin), ctypes.byref(xc), ctypes.byref(yc)))
+    return vmin.value, xc.value, yc.value
+
+
+def lbm_batch_probe(b, x, y, every: int, dev_series, cap: int) -> None:
+    ax = np.ascontiguousarray(x, dtype=np.float64)
+    ay = np.ascontiguousarray(y, dtype=np.float64)
+    _bcheck(b, library().lbm_batch_probe(b, ax.ctypes.data, ay.ctypes.data, int(every), _ptr(dev_series), int(cap)))
+
+
+def lbm_batch_info(b, i: int) -> lbm_info:
+    info = lbm_info()
+    _bcheck(b, library().lbm_batch_info(b, i, ctypes.byref(info)))
+    return info
+
+
+def lbm_batch_set_barrier_limit(b, seconds: float, absent_block: int = -1) -> None:
+    _bcheck(b, library().lbm_batch_set_barrier_limit(b, float(seconds), int(absent_block)))

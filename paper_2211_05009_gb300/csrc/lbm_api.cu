@@ -119,6 +119,8 @@ struct lbm_ctx {
         a.plane = plane;
         a.omega = 1.0 / tau;
         a.U = U;
+        a.omega_f = (float)a.omega;
+        a.U_f = (float)U;
         a.corner_moving = (flags & LBM_FLAG_LID_CORNERS_MOVING) ? 1 : 0;
         a.s = s;
         a.state = d_state;

@@ -1,0 +1,711 @@
+// lbm_batch.cu -- a sweep of independent cavities of uneven sizes (each its own nx, ny, Re, U) in
+// one persistent kernel: the batched form of the step of Xiang & Shi (arXiv 2211.05009) Sec. 2,
+// used for the Re x Ar state survey of Sec. 3.3 (Fig. 17).
+//
+// Work decomposition: every cavity is cut into items of one warp-wide column strip (32*V nodes)
+// by R rows; items of all active cavities are numbered consecutively and the warps of the grid
+// take them round-robin, so small and large cavities share the GPU.  A launch runs up to one
+// checkpoint interval (100 steps); steps are separated by a grid barrier.  The launch is
+// cooperative (all blocks resident) and every barrier wait is bounded by a clock limit: when it
+// runs out the kernel sets an error word and returns, and the host reports LBM_ETIMEOUT.
+// At each checkpoint (Sec. 2.2 iii) every cavity gets its own Eq. 6 residual and mass (fixed-order
+// FP64 sums of per-item partials), cavities whose residual fell below tol -- or that reached the
+// step cap -- retire, and the active list is compacted so retired cavities cost nothing.
+// The populations of both pools are read and written within one launch, so all loads of them go
+// through L2 (ld.global.cg), never the read-only path.
+#include <cuda/atomic>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+#include "lbm_step_kernel.cuh"
+
+namespace lbm {
+
+constexpr int kBatchThreads = 128;
+constexpr int kBatchR = 4;  // rows per item
+
+struct BatchCav {
+    long long off;       // population offset (storage elements) in each pool
+    long long snap_off;  // snapshot offset (arithmetic-type elements)
+    long long pitch, plane;
+    int nx, ny;
+    double omega, U;
+    float omega_f, U_f;
+    int corner_moving;
+    int strips, rowgroups, items, item0;
+    // one observing point per cavity (Sec. 3.3)
+    int px, py, every;
+    long long cap;
+    double* series;
+};
+
+struct BatchState {
+    long long step;  // global step of the active cavities
+    int n_active;
+    int err;         // 1: a barrier wait ran out
+    unsigned bar_count, bar_gen;
+    int active[LBM_BATCH_MAX];
+    int prefix[LBM_BATCH_MAX + 1];  // exclusive prefix of item counts over the active list
+    long long done_at[LBM_BATCH_MAX];  // global step of a retired cavity's state (-1: active)
+    long long probe_start[LBM_BATCH_MAX];
+    double residual[LBM_BATCH_MAX], mass[LBM_BATCH_MAX];
+    int status[LBM_BATCH_MAX];  // 0 active, 1 converged, 2 step cap, 3 non-finite
+};
+
+struct BatchArgs {
+    void* pool[2];
+    void* snap;
+    const BatchCav* cavs;
+    BatchState* st;
+    double* partials;  // 3 per item, full numbering
+    int nsteps;
+    double tol;           // retire when residual < tol (tol <= 0: never)
+    long long max_step;   // retire a cavity at this global step (<= 0: never)
+    long long spin_limit; // barrier wait limit in clock cycles
+    int absent_block;     // test hook: this block leaves at the first barrier (-1: none)
+};
+
+// Grid barrier with a bounded wait.  Returns false (and sets st->err) if the wait ran out or any
+// block reported a timeout; callers then return.
+__device__ __forceinline__ bool grid_barrier(BatchState* st, long long limit) {
+    __shared__ int ok_sh;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> gen(st->bar_gen);
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(st->bar_count);
+        cuda::atomic_ref<int, cuda::thread_scope_device> err(st->err);
+        const unsigned g = gen.load(cuda::memory_order_acquire);
+        const unsigned arrived = cnt.fetch_add(1u, cuda::memory_order_acq_rel) + 1u;
+        if (arrived == gridDim.x) {
+            cnt.store(0u, cuda::memory_order_relaxed);
+            gen.store(g + 1u, cuda::memory_order_release);
+        } else {
+            const long long t0 = clock64();
+            while (gen.load(cuda::memory_order_acquire) == g) {
+                if (err.load(cuda::memory_order_relaxed) || clock64() - t0 > limit) {
+                    err.store(1, cuda::memory_order_relaxed);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        if (err.load(cuda::memory_order_acquire)) ok = 0;
+        __threadfence();
+        ok_sh = ok;
+    }
+    __syncthreads();
+    return ok_sh != 0;
+}
+
+template <typename S, bool SHIFTED, int V>
+__global__ void __launch_bounds__(kBatchThreads, 4) k_batch(const BatchArgs a) {
+    using C = typename St<S>::C;
+    __shared__ int s_active[LBM_BATCH_MAX];
+    __shared__ int s_prefix[LBM_BATCH_MAX + 1];
+    __shared__ int s_n;
+    BatchState* st = a.st;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    constexpr int W = kBatchThreads / 32;
+    const long long gwarp = (long long)blockIdx.x * W + warp;
+    const long long nwarps = (long long)gridDim.x * W;
+    const long long step0 = __ldcg(&st->step);
+
+    for (int s = 0; s < a.nsteps; ++s) {
+        const long long step = step0 + s;
+        const bool reduce = (step + 1) % kInterval == 0;
+        // the active list (changes only at checkpoints, behind barriers)
+        if (threadIdx.x == 0) s_n = __ldcg(&st->n_active);
+        __syncthreads();
+        const int n = s_n;
+        for (int k = threadIdx.x; k <= n; k += blockDim.x) {
+            if (k < n) s_active[k] = __ldcg(&st->active[k]);
+            s_prefix[k] = __ldcg(&st->prefix[k]);
+        }
+        __syncthreads();
+        const int n_items = s_prefix[n];
+        const S* src_pool = static_cast<const S*>(a.pool[step & 1]);
+        S* dst_pool = static_cast<S*>(a.pool[(step + 1) & 1]);
+        for (long long item = gwarp; item < n_items; item += nwarps) {
+            int lo = 0, hi = n - 1;  // largest k with prefix[k] <= item
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_prefix[mid] <= item) lo = mid; else hi = mid - 1;
+            }
+            const BatchCav& cd = a.cavs[s_active[lo]];
+            const int local = (int)(item - s_prefix[lo]);
+            const int strip = local % cd.strips, rg = local / cd.strips;
+            CavityView<C> cv;
+            cv.nx = cd.nx;
+            cv.ny = cd.ny;
+            cv.pitch = cd.pitch;
+            cv.plane = cd.plane;
+            cv.omega = sizeof(C) == 4 ? C(cd.omega_f) : C(cd.omega);
+            cv.Ulid = sizeof(C) == 4 ? C(cd.U_f) : C(cd.U);
+            cv.corner_moving = cd.corner_moving;
+            ProbeOne pr;
+            pr.n_ = cd.series ? 1 : 0;
+            pr.px_ = cd.px;
+            pr.py_ = cd.py;
+            pr.every_ = cd.every > 0 ? cd.every : 1;
+            pr.start_ = cd.series ? __ldcg(&st->probe_start[s_active[lo]]) : 0;
+            pr.cap_ = cd.cap > 0 ? cd.cap : 1;
+            pr.series_ = cd.series;
+            const S* src = src_pool + cd.off;
+            S* dst = dst_pool + cd.off;
+            C* snap = static_cast<C*>(a.snap) + cd.snap_off;
+            const int x0 = (strip * 32 + lane) * V;
+            C a0 = C(0), a1 = C(0), a2 = C(0);
+            for (int r = 0; r < kBatchR; ++r) {
+                const int y = rg * kBatchR + r;
+                if (y >= cd.ny) break;
+                if (reduce)
+                    step_row<S, SHIFTED, true, V, 2>(src, dst, cv, lane, x0, y, snap, pr,
+                                                     [step]() { return step + 1; }, a0, a1, a2);
+                else
+                    step_row<S, SHIFTED, false, V, 2>(src, dst, cv, lane, x0, y, snap, pr,
+                                                      [step]() { return step + 1; }, a0, a1, a2);
+            }
+            if (reduce) {
+                const double p0 = warp_sum(double(a0)), p1 = warp_sum(double(a1)), p2 = warp_sum(double(a2));
+                if (lane == 0) {
+                    double* p = a.partials + 3ll * (cd.item0 + local);
+                    p[0] = p0;
+                    p[1] = p1;
+                    p[2] = p2;
+                }
+            }
+        }
+        if (a.absent_block == (int)blockIdx.x && s == 0) return;  // test hook: never arrives
+        if (!grid_barrier(st, a.spin_limit)) return;
+        if (!reduce) continue;
+
+        // checkpoint: per-cavity Eq. 6 and mass, in a fixed order
+        __shared__ double red[3][kBatchThreads];
+        for (int k = blockIdx.x; k < n; k += gridDim.x) {
+            const int c = s_active[k];
+            const BatchCav& cd = a.cavs[c];
+            double q0 = 0.0, q1 = 0.0, q2 = 0.0;
+            for (int i = threadIdx.x; i < cd.items; i += blockDim.x) {
+                const double* p = a.partials + 3ll * (cd.item0 + i);
+                q0 += __ldcg(p);
+                q1 += __ldcg(p + 1);
+                q2 += __ldcg(p + 2);
+            }
+            red[0][threadIdx.x] = q0;
+            red[1][threadIdx.x] = q1;
+            red[2][threadIdx.x] = q2;
+            __syncthreads();
+            for (int o = kBatchThreads / 2; o > 0; o >>= 1) {
+                if (threadIdx.x < o)
+                    for (int m = 0; m < 3; ++m) red[m][threadIdx.x] += red[m][threadIdx.x + o];
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) {
+                const double r = sqrt(red[1][0] / red[2][0]);
+                const double mass = (double)cd.nx * cd.ny + red[0][0];
+                st->residual[c] = r;
+                st->mass[c] = mass;
+                int status = 0;
+                if (!isfinite(r) || !isfinite(mass)) status = 3;
+                else if (a.tol > 0.0 && r < a.tol) status = 1;
+                else if (a.max_step > 0 && step + 1 >= a.max_step) status = 2;
+                st->status[c] = status;
+                if (status) st->done_at[c] = step + 1;
+            }
+            __syncthreads();
+        }
+        if (!grid_barrier(st, a.spin_limit)) return;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {  // compact the active list
+            int m = 0, acc = 0;
+            for (int k = 0; k < n; ++k) {
+                const int c = s_active[k];
+                if (__ldcg(&st->status[c]) == 0) {
+                    st->active[m] = c;
+                    st->prefix[m] = acc;
+                    acc += a.cavs[c].items;
+                    ++m;
+                }
+            }
+            st->prefix[m] = acc;
+            st->n_active = m;
+        }
+        if (!grid_barrier(st, a.spin_limit)) return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->step = step0 + a.nsteps;
+}
+
+template <typename S, bool SHIFTED>
+static cudaError_t launch_batch_t(const BatchArgs& a, int blocks, cudaStream_t st) {
+    constexpr int V = sizeof(S) == 8 ? 2 : 4;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(kBatchThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_batch<S, SHIFTED, V>, a);
+}
+
+template <typename S, bool SHIFTED>
+static int batch_blocks_t() {
+    constexpr int V = sizeof(S) == 8 ? 2 : 4;
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<S, SHIFTED, V>, kBatchThreads, 0) != cudaSuccess) return 0;
+    return per * sms;
+}
+
+#define LBM_BATCH_DISPATCH(dtype, CALL)                                              \
+    switch (dtype) {                                                                 \
+        case 0: { using S = double; constexpr bool SH = true; CALL; }               \
+        case 1: { using S = float; constexpr bool SH = false; CALL; }               \
+        case 2: { using S = float; constexpr bool SH = true; CALL; }                \
+        case 3: { using S = __half; constexpr bool SH = true; CALL; }               \
+        case 4: { using S = __nv_bfloat16; constexpr bool SH = true; CALL; }        \
+        default: break;                                                              \
+    }
+
+static cudaError_t launch_batch(int dtype, const BatchArgs& a, int blocks, cudaStream_t st) {
+    LBM_BATCH_DISPATCH(dtype, return (launch_batch_t<S, SH>(a, blocks, st)));
+    return cudaErrorInvalidValue;
+}
+
+static int batch_blocks(int dtype) {
+    LBM_BATCH_DISPATCH(dtype, return (batch_blocks_t<S, SH>()));
+    return 0;
+}
+
+}  // namespace lbm
+
+using namespace lbm;
+
+namespace {
+std::string bfmt(const char* f, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, f);
+    vsnprintf(buf, sizeof buf, f, ap);
+    va_end(ap);
+    return buf;
+}
+thread_local std::string g_batch_create_error;
+}  // namespace
+
+struct lbm_batch {
+    int n = 0, dtype = 0;
+    std::vector<BatchCav> cavs;
+    std::vector<double> tau;
+    void* pool[2] = {nullptr, nullptr};
+    void* snap = nullptr;
+    BatchCav* d_cavs = nullptr;
+    BatchState* d_state = nullptr;
+    BatchState* h_state = nullptr;  // pinned
+    double* partials = nullptr;
+    double* psi_scratch = nullptr;
+    size_t psi_doubles = 0;
+    DevState* d_ext = nullptr;  // stream-function results
+    DevState* h_ext = nullptr;  // pinned
+    int total_items = 0;
+    int blocks = 0;
+    long long step = 0;  // host mirror of the active step
+    double spin_limit_s = 2.0;
+    cudaStream_t stream = nullptr;
+    size_t device_bytes = 0;
+    std::string err;
+
+    int fail(int code, const std::string& m) {
+        err = m;
+        return code;
+    }
+    int cuda(cudaError_t e, const char* what) {
+        if (e == cudaSuccess) return LBM_OK;
+        err = bfmt("%s: %s", what, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+    }
+    void* dalloc(size_t bytes) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        device_bytes += bytes;
+        return p;
+    }
+    int sync() { return cuda(cudaStreamSynchronize(stream), "stream synchronize"); }
+
+    long long cavity_step(int i) const {
+        const long long d = h_state->done_at[i];
+        return d >= 0 ? d : step;
+    }
+    FieldArgs field(int i) const {
+        FieldArgs a{};
+        const BatchCav& c = cavs[i];
+        const size_t es = storage_bytes(dtype);
+        a.f = (char*)pool[cavity_step(i) & 1] + c.off * es;
+        a.nx = c.nx;
+        a.ny = c.ny;
+        a.pitch = c.pitch;
+        a.plane = c.plane;
+        a.U = c.U;
+        a.corner_moving = c.corner_moving;
+        return a;
+    }
+
+    // Advance every active cavity by n steps (retiring per tol / max_step at checkpoints).
+    int run(long long n, double tol, long long max_step) {
+        int rc = LBM_OK;
+        long long clock_khz = 0;
+        {
+            int dev = 0, khz = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+            clock_khz = khz > 0 ? khz : 2000000;
+        }
+        while (n > 0 && !rc) {
+            const long long chunk = std::min<long long>(n, kInterval - step % kInterval);
+            BatchArgs a{};
+            a.pool[0] = pool[0];
+            a.pool[1] = pool[1];
+            a.snap = snap;
+            a.cavs = d_cavs;
+            a.st = d_state;
+            a.partials = partials;
+            a.nsteps = (int)chunk;
+            a.tol = tol;
+            a.max_step = max_step;
+            a.spin_limit = (long long)(spin_limit_s * clock_khz * 1000.0);
+            a.absent_block = absent_block;
+            rc = cuda(launch_batch(dtype, a, blocks, stream), "batch kernel launch");
+            if (rc) return rc;
+            absent_block = -1;
+            step += chunk;
+            n -= chunk;
+        }
+        return rc;
+    }
+    int absent_block = -1;
+
+    int pull_state() {
+        int rc = cuda(cudaMemcpyAsync(h_state, d_state, sizeof(BatchState), cudaMemcpyDeviceToHost, stream), "state copy");
+        if (!rc) rc = sync();
+        if (!rc && h_state->err) {
+            // re-arm the barrier so the batch can be used again; the populations of the
+            // interrupted launch are partly advanced and must not be trusted
+            h_state->err = 0;
+            h_state->bar_count = 0;
+            cudaMemcpyAsync(&d_state->err, &h_state->err, sizeof(int), cudaMemcpyHostToDevice, stream);
+            cudaMemcpyAsync(&d_state->bar_count, &h_state->bar_count, sizeof(unsigned), cudaMemcpyHostToDevice, stream);
+            sync();
+            step = h_state->step;
+            return fail(LBM_ETIMEOUT, "a grid barrier wait of the batch kernel ran out");
+        }
+        if (!rc) step = h_state->step;
+        return rc;
+    }
+};
+
+extern "C" int lbm_batch_create(int n, const int* nx, const int* ny, const double* Re, const double* U,
+                                lbm_dtype dtype, lbm_batch** out) {
+    g_batch_create_error.clear();
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    auto bad = [&](const std::string& m) {
+        g_batch_create_error = m;
+        return LBM_EINVAL;
+    };
+    if (n < 1 || n > LBM_BATCH_MAX) return bad(bfmt("batch of %d cavities: need 1..%d", n, LBM_BATCH_MAX));
+    if (!nx || !ny || !Re || !U) return bad("NULL parameter array");
+    if ((int)dtype < 0 || (int)dtype > 4) return bad("unknown dtype");
+    for (int i = 0; i < n; ++i) {
+        if (nx[i] < 3 || ny[i] < 3) return bad(bfmt("cavity %d: grid %d x %d, need >= 3", i, nx[i], ny[i]));
+        const double tau = 3.0 * U[i] * nx[i] / Re[i] + 0.5;
+        if (!(Re[i] > 0) || !(tau > 0.5) || !std::isfinite(tau)) return bad(bfmt("cavity %d: Re/U give tau = %g", i, tau));
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        g_batch_create_error = "no CUDA device available (the library has no CPU path)";
+        return LBM_ECUDA;
+    }
+    lbm_batch* b = new lbm_batch();
+    b->n = n;
+    b->dtype = (int)dtype;
+    const int V = storage_bytes(b->dtype) == 8 ? 2 : 4;
+    long long off = 0, soff = 0;
+    int item0 = 0;
+    size_t max_psi = 0;
+    for (int i = 0; i < n; ++i) {
+        BatchCav c{};
+        c.nx = nx[i];
+        c.ny = ny[i];
+        c.pitch = row_pitch(b->dtype, nx[i]);
+        c.plane = c.pitch * ny[i];
+        const double tau = 3.0 * U[i] * nx[i] / Re[i] + 0.5;  // Re = U nx / nu, Eq. 5
+        b->tau.push_back(tau);
+        c.omega = 1.0 / tau;
+        c.U = U[i];
+        c.omega_f = (float)c.omega;
+        c.U_f = (float)U[i];
+        c.off = off;
+        c.snap_off = soff;
+        c.strips = (int)(c.pitch / (32 * V));
+        c.rowgroups = (ny[i] + kBatchR - 1) / kBatchR;
+        c.items = c.strips * c.rowgroups;
+        c.item0 = item0;
+        c.series = nullptr;
+        off += 9 * c.plane;
+        off = (off + 63) / 64 * 64;  // keep every cavity 512-byte aligned
+        soff += 2 * c.plane;
+        item0 += c.items;
+        max_psi = std::max(max_psi, psi_scratch_doubles(nx[i], ny[i]));
+        b->cavs.push_back(c);
+    }
+    b->total_items = item0;
+    auto fail = [&](int code, const std::string& m) {
+        g_batch_create_error = m.empty() ? b->err : m;
+        lbm_batch_destroy(b);
+        return code;
+    };
+    const size_t es = storage_bytes(b->dtype);
+    for (int p = 0; p < 2; ++p)
+        if (!(b->pool[p] = b->dalloc((size_t)off * es))) return fail(LBM_ENOMEM, bfmt("population pool of %zu bytes", (size_t)off * es));
+    b->snap = b->dalloc((size_t)soff * arith_bytes(b->dtype));
+    b->d_cavs = (BatchCav*)b->dalloc(sizeof(BatchCav) * n);
+    b->d_state = (BatchState*)b->dalloc(sizeof(BatchState));
+    b->partials = (double*)b->dalloc(sizeof(double) * 3 * (size_t)b->total_items);
+    b->psi_doubles = max_psi;
+    b->psi_scratch = (double*)b->dalloc(sizeof(double) * max_psi);
+    b->d_ext = (DevState*)b->dalloc(sizeof(DevState));
+    if (!b->snap || !b->d_cavs || !b->d_state || !b->partials || !b->psi_scratch || !b->d_ext) return fail(LBM_ENOMEM, "batch scratch allocation");
+    int rc = b->cuda(cudaMallocHost(&b->h_state, sizeof(BatchState)), "pinned host allocation");
+    if (!rc) rc = b->cuda(cudaMallocHost(&b->h_ext, sizeof(DevState)), "pinned host allocation");
+    if (rc) return fail(rc, "");
+    b->blocks = batch_blocks(b->dtype);
+    if (b->blocks <= 0) return fail(LBM_ECUDA, "batch kernel occupancy query failed");
+    // initial state (Sec. 2.2 i) for every cavity, in both pools
+    for (int i = 0; i < n && !rc; ++i)
+        for (int p = 0; p < 2 && !rc; ++p) {
+            FieldArgs a{};
+            a.f = (char*)b->pool[p] + b->cavs[i].off * es;
+            a.nx = nx[i];
+            a.ny = ny[i];
+            a.pitch = b->cavs[i].pitch;
+            a.plane = b->cavs[i].plane;
+            a.U = U[i];
+            a.corner_moving = 0;
+            void* sp = (char*)b->snap + b->cavs[i].snap_off * arith_bytes(b->dtype);
+            rc = b->cuda(launch_init(b->dtype, a, sp, b->stream), "init kernel launch");
+        }
+    if (rc) return fail(rc, "");
+    BatchState* h = b->h_state;
+    memset(h, 0, sizeof(BatchState));
+    h->n_active = n;
+    int acc = 0;
+    for (int i = 0; i < n; ++i) {
+        h->active[i] = i;
+        h->prefix[i] = acc;
+        acc += b->cavs[i].items;
+        h->done_at[i] = -1;
+    }
+    h->prefix[n] = acc;
+    rc = b->cuda(cudaMemcpyAsync(b->d_cavs, b->cavs.data(), sizeof(BatchCav) * n, cudaMemcpyHostToDevice, b->stream), "descriptor upload");
+    if (!rc) rc = b->cuda(cudaMemcpyAsync(b->d_state, h, sizeof(BatchState), cudaMemcpyHostToDevice, b->stream), "state upload");
+    if (!rc) rc = b->sync();
+    if (rc) return fail(rc, "");
+    *out = b;
+    return LBM_OK;
+}
+
+extern "C" void lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    for (void* p : {b->pool[0], b->pool[1], b->snap, (void*)b->d_cavs, (void*)b->d_state, (void*)b->partials, (void*)b->psi_scratch, (void*)b->d_ext})
+        if (p) cudaFree(p);
+    if (b->h_state) cudaFreeHost(b->h_state);
+    if (b->h_ext) cudaFreeHost(b->h_ext);
+    delete b;
+}
+
+extern "C" const char* lbm_batch_last_error(const lbm_batch* b) {
+    return b ? b->err.c_str() : g_batch_create_error.c_str();
+}
+
+extern "C" int lbm_batch_set_stream(lbm_batch* b, void* stream) {
+    if (!b) return LBM_EINVAL;
+    int rc = b->sync();
+    b->stream = (cudaStream_t)stream;
+    return rc;
+}
+
+extern "C" int lbm_batch_step(lbm_batch* b, long n) {
+    if (!b) return LBM_EINVAL;
+    if (n < 0) return b->fail(LBM_EINVAL, "n < 0");
+    int rc = b->run(n, -1.0, 0);
+    if (!rc) rc = b->pull_state();
+    return rc;
+}
+
+extern "C" int lbm_batch_run_to_residual(lbm_batch* b, double tol, long max_steps, long* steps_done) {
+    if (!b) return LBM_EINVAL;
+    if (!(tol > 0) || max_steps < 0) return b->fail(LBM_EINVAL, "need tol > 0 and max_steps >= 0");
+    const long long start = b->step;
+    const long long cap = start + max_steps;
+    int rc = LBM_OK;
+    // run in chunks of 10 checkpoint intervals, stopping early once every cavity retired
+    while (!rc && b->step < cap) {
+        const long long chunk = std::min<long long>(cap - b->step, 10 * kInterval);
+        rc = b->run(chunk, tol, cap);
+        if (!rc) rc = b->pull_state();
+        if (!rc && b->h_state->n_active == 0) break;
+    }
+    if (rc) return rc;
+    bool all = true;
+    for (int i = 0; i < b->n; ++i) {
+        const long long d = b->h_state->done_at[i];
+        if (steps_done) steps_done[i] = (long)((d >= 0 ? d : b->step) - start);
+        if (b->h_state->status[i] == 3) return b->fail(LBM_EDIVERGED, bfmt("cavity %d diverged", i));
+        if (b->h_state->status[i] != 1) all = false;
+    }
+    return all ? LBM_OK : b->fail(LBM_ENOTREADY, "some cavities did not reach tol within max_steps");
+}
+
+extern "C" int lbm_batch_residual(lbm_batch* b, double* r, int* status) {
+    if (!b || !r) return LBM_EINVAL;
+    int rc = b->pull_state();
+    if (rc) return rc;
+    for (int i = 0; i < b->n; ++i) {
+        r[i] = b->h_state->residual[i];
+        if (status) status[i] = b->h_state->status[i];
+    }
+    return LBM_OK;
+}
+
+extern "C" int lbm_batch_cavity_steps(lbm_batch* b, long* steps) {
+    if (!b || !steps) return LBM_EINVAL;
+    int rc = b->pull_state();
+    if (rc) return rc;
+    for (int i = 0; i < b->n; ++i) steps[i] = (long)b->cavity_step(i);
+    return LBM_OK;
+}
+
+extern "C" int lbm_batch_moments(lbm_batch* b, int i, double* rho, double* ux, double* uy) {
+    if (!b || i < 0 || i >= b->n) return b ? b->fail(LBM_EINVAL, "no such cavity") : LBM_EINVAL;
+    int rc = b->pull_state();
+    if (rc) return rc;
+    const size_t bytes = (size_t)b->cavs[i].nx * b->cavs[i].ny * sizeof(double);
+    double* outs[3] = {rho, ux, uy};
+    for (int k = 0; k < 3; ++k) {
+        if (!outs[k]) continue;
+        cudaPointerAttributes at{};
+        cudaError_t e = cudaPointerGetAttributes(&at, outs[k]);
+        if (e != cudaSuccess) cudaGetLastError();
+        if (!(e == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)))
+            return b->fail(LBM_EINVAL, "lbm_batch_moments needs device buffers");
+    }
+    (void)bytes;
+    rc = b->cuda(launch_moments(b->dtype, b->field(i), rho, ux, uy, b->stream), "moments launch");
+    if (!rc) rc = b->sync();
+    return rc;
+}
+
+extern "C" int lbm_batch_get_populations(lbm_batch* b, int i, double* f) {
+    if (!b || i < 0 || i >= b->n || !f) return b ? b->fail(LBM_EINVAL, "bad arguments") : LBM_EINVAL;
+    int rc = b->pull_state();
+    if (rc) return rc;
+    cudaPointerAttributes at{};
+    cudaError_t e = cudaPointerGetAttributes(&at, f);
+    if (e != cudaSuccess) cudaGetLastError();
+    if (!(e == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)))
+        return b->fail(LBM_EINVAL, "lbm_batch_get_populations needs a device buffer");
+    rc = b->cuda(launch_get_populations(b->dtype, b->field(i), f, b->stream), "get_populations launch");
+    if (!rc) rc = b->sync();
+    return rc;
+}
+
+extern "C" int lbm_batch_stream_function(lbm_batch* b, int i, double* psi, double* psi_min, double* xc, double* yc) {
+    if (!b || i < 0 || i >= b->n) return b ? b->fail(LBM_EINVAL, "no such cavity") : LBM_EINVAL;
+    int rc = b->pull_state();
+    if (rc) return rc;
+    const BatchCav& c = b->cavs[i];
+    if (psi) {
+        cudaPointerAttributes at{};
+        cudaError_t e = cudaPointerGetAttributes(&at, psi);
+        if (e != cudaSuccess) cudaGetLastError();
+        if (!(e == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)))
+            return b->fail(LBM_EINVAL, "lbm_batch_stream_function needs a device psi buffer");
+    }
+    rc = b->cuda(launch_stream_function(b->dtype, b->field(i), psi, 0, c.nx, 0, c.ny, b->psi_scratch, b->d_ext, b->stream), "stream function launch");
+    if (!rc) rc = b->cuda(cudaMemcpyAsync(b->h_ext, b->d_ext, sizeof(DevState), cudaMemcpyDeviceToHost, b->stream), "extrema copy");
+    if (!rc) rc = b->sync();
+    if (rc) return rc;
+    if (psi_min) *psi_min = b->h_ext->ext[0];
+    if (xc) *xc = b->h_ext->ext[1] / c.nx;
+    if (yc) *yc = b->h_ext->ext[2] / c.nx;
+    return std::isfinite(b->h_ext->ext[0]) ? LBM_OK : b->fail(LBM_EDIVERGED, "non-finite stream function");
+}
+
+extern "C" int lbm_batch_probe(lbm_batch* b, const double* x, const double* y, int every, double* dev_series, long cap) {
+    if (!b || !x || !y || !dev_series || every < 1 || cap < 1) return b ? b->fail(LBM_EINVAL, "bad probe arguments") : LBM_EINVAL;
+    cudaPointerAttributes at{};
+    cudaError_t e = cudaPointerGetAttributes(&at, dev_series);
+    if (e != cudaSuccess) cudaGetLastError();
+    if (!(e == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)))
+        return b->fail(LBM_EINVAL, "probe series must be device memory");
+    int rc = b->pull_state();
+    if (rc) return rc;
+    for (int i = 0; i < b->n; ++i) {
+        BatchCav& c = b->cavs[i];
+        int px = (int)std::floor(x[i] * c.nx + 0.5), py = (int)std::floor(y[i] * c.nx + 0.5);
+        c.px = px < 0 ? 0 : (px >= c.nx ? c.nx - 1 : px);
+        c.py = py < 0 ? 0 : (py >= c.ny ? c.ny - 1 : py);
+        c.every = every;
+        c.cap = cap;
+        c.series = dev_series + 2ll * cap * i;
+        b->h_state->probe_start[i] = b->cavity_step(i);
+    }
+    rc = b->cuda(cudaMemcpyAsync(b->d_cavs, b->cavs.data(), sizeof(BatchCav) * b->n, cudaMemcpyHostToDevice, b->stream), "descriptor upload");
+    if (!rc) rc = b->cuda(cudaMemcpyAsync(b->d_state->probe_start, b->h_state->probe_start, sizeof(long long) * b->n, cudaMemcpyHostToDevice, b->stream), "probe start upload");
+    if (!rc) rc = b->sync();
+    return rc;
+}
+
+extern "C" int lbm_batch_info(lbm_batch* b, int i, lbm_info* info) {
+    if (!b || !info || i < 0 || i >= b->n) return LBM_EINVAL;
+    const BatchCav& c = b->cavs[i];
+    info->nx = c.nx;
+    info->ny = c.ny;
+    info->pitch = (long)c.pitch;
+    info->tau = b->tau[i];
+    info->nu = (b->tau[i] - 0.5) / 3.0;
+    info->U = c.U;
+    info->Re = c.U * c.nx / info->nu;
+    info->dtype = b->dtype;
+    info->flags = 0;
+    info->step = (long)b->cavity_step(i);
+    info->device_bytes = b->device_bytes;
+    info->launch_config = b->blocks;
+    return LBM_OK;
+}
+
+extern "C" int lbm_batch_set_barrier_limit(lbm_batch* b, double seconds, int absent_block) {
+    if (!b || !(seconds > 0)) return LBM_EINVAL;
+    b->spin_limit_s = seconds;
+    b->absent_block = absent_block;
+    return LBM_OK;
+}

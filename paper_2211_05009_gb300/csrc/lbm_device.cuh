@@ -98,6 +98,7 @@ struct StepArgs {
     long long plane;  // pitch * ny
     double omega;     // 1/tau
     double U;         // lid speed
+    float omega_f, U_f;  // the same in FP32 (no FP64 conversion in FP32 kernels)
     int corner_moving;
     int s;            // steps since the last checkpoint (0..99) of the state being advanced
     DevState* state;

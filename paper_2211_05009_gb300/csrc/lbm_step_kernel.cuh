@@ -32,11 +32,15 @@ template <> struct Raw<16> { using T = uint4; };
 template <> struct Raw<8> { using T = uint2; };
 template <> struct Raw<4> { using T = unsigned int; };
 
-// Read-only vector load; HINT = 1 adds an L2 256-byte prefetch and skips L1 allocation.
+// Vector load.  HINT 0: read-only path; 1: read-only with an L2 256-byte prefetch, no L1
+// allocation; 2: coherent L2 load (ld.global.cg) for kernels that also write the array they read
+// from across a grid barrier (the read-only path may serve stale lines there).
 template <typename T, int HINT>
 __device__ __forceinline__ T ldg_vec(const T* p) {
     if constexpr (HINT == 0) {
         return __ldg(p);
+    } else if constexpr (HINT == 2) {
+        return __ldcg(p);
     } else if constexpr (sizeof(T) == 16) {
         uint4 r;
         asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0, %1, %2, %3}, [%4];"
@@ -64,7 +68,7 @@ __device__ __forceinline__ void vload_n(const S* __restrict__ p, typename St<S>:
 }
 
 // V values of a plain arithmetic-type array (the Eq. 6 snapshot), in 16-byte pieces.
-template <typename C, int V>
+template <typename C, int V, bool COHERENT = false>
 __device__ __forceinline__ void cload(const C* p, C (&out)[V]) {
     constexpr int B = V * sizeof(C) < 16 ? V * sizeof(C) : 16;
     constexpr int PER = B / sizeof(C);
@@ -72,7 +76,10 @@ __device__ __forceinline__ void cload(const C* p, C (&out)[V]) {
 #pragma unroll
     for (int k = 0; k < V; k += PER) {
         union { T u; C c[PER]; } b;
-        b.u = *reinterpret_cast<const T*>(p + k);
+        if constexpr (COHERENT)
+            b.u = __ldcg(reinterpret_cast<const T*>(p + k));
+        else
+            b.u = *reinterpret_cast<const T*>(p + k);
 #pragma unroll
         for (int i = 0; i < PER; ++i) out[k + i] = b.c[i];
     }
@@ -100,6 +107,22 @@ __device__ __forceinline__ void vstore_n(S* __restrict__ p, const typename St<S>
     *reinterpret_cast<T*>(p) = b.u;
 }
 
+// Scalar load of one storage element, coherent at L2 when HINT == 2.
+template <typename S, int HINT>
+__device__ __forceinline__ typename St<S>::C lds(const S* p) {
+    if constexpr (HINT == 2) {
+        if constexpr (sizeof(S) == 8) return St<S>::to(__ldcg(reinterpret_cast<const double*>(p)));
+        else if constexpr (sizeof(S) == 4) return St<S>::to(__ldcg(reinterpret_cast<const float*>(p)));
+        else {
+            union { unsigned short u; S s; } b;
+            b.u = __ldcg(reinterpret_cast<const unsigned short*>(p));
+            return St<S>::to(b.s);
+        }
+    } else {
+        return St<S>::to(*p);
+    }
+}
+
 // Pull one population row segment: out[i] = value at (x0 + i - DX), DX = c_x of the direction.
 template <typename S, bool SHIFTED, int V, int DX, int HINT>
 __device__ __forceinline__ void pull_row(const S* __restrict__ p, int lane, int x0, long long pitch,
@@ -112,13 +135,13 @@ __device__ __forceinline__ void pull_row(const S* __restrict__ p, int lane, int 
         for (int i = 0; i < V; ++i) out[i] = v[i];
     } else if constexpr (DX == 1) {
         C left = __shfl_up_sync(kFull, v[V - 1], 1);
-        if (lane == 0) left = (x0 > 0) ? St<S>::to(p[-1]) : v[0];
+        if (lane == 0) left = (x0 > 0) ? lds<S, HINT>(p - 1) : v[0];
         out[0] = left;
 #pragma unroll
         for (int i = 1; i < V; ++i) out[i] = v[i - 1];
     } else {
         C right = __shfl_down_sync(kFull, v[0], 1);
-        if (lane == 31) right = (x0 + V < pitch) ? St<S>::to(p[V]) : v[V - 1];
+        if (lane == 31) right = (x0 + V < pitch) ? lds<S, HINT>(p + V) : v[V - 1];
 #pragma unroll
         for (int i = 0; i < V - 1; ++i) out[i] = v[i + 1];
         out[V - 1] = right;
@@ -187,9 +210,181 @@ __device__ __forceinline__ void pull_segment(const S* __restrict__ src, int lane
         const long long xf = nx - 2;
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
-            const C v = St<S>::to(src[j * plane + (long long)(yc - cy(j)) * pitch + (xf - cx(j))]);
+            const C v = lds<S, HINT>(src + j * plane + (long long)(yc - cy(j)) * pitch + (xf - cx(j)));
             f[j][0] = SHIFTED ? v : v - C(wd(j));
         }
+    }
+}
+
+// Observing points as the row step sees them: the up-to-four probes of a single cavity
+// (kernel parameter space) or the one probe of a batched cavity (registers).
+struct ProbeList {
+    const ProbeSet& p;
+    __device__ int n() const { return p.n; }
+    __device__ int px(int q) const { return p.px[q]; }
+    __device__ int py(int q) const { return p.py[q]; }
+    __device__ int every(int q) const { return p.every[q]; }
+    __device__ long long start(int q) const { return p.start[q]; }
+    __device__ long long cap(int q) const { return p.cap[q]; }
+    __device__ double* series(int q) const { return p.series[q]; }
+};
+struct ProbeOne {
+    int n_, px_, py_, every_;
+    long long start_, cap_;
+    double* series_;
+    __device__ int n() const { return n_; }
+    __device__ int px(int) const { return px_; }
+    __device__ int py(int) const { return py_; }
+    __device__ int every(int) const { return every_; }
+    __device__ long long start(int) const { return start_; }
+    __device__ long long cap(int) const { return cap_; }
+    __device__ double* series(int) const { return series_; }
+};
+
+// Geometry and parameters of one cavity as the row step sees them.
+template <typename C>
+struct CavityView {
+    int nx, ny;
+    long long pitch, plane;
+    C omega, Ulid;
+    int corner_moving;
+};
+
+// One time step for the V nodes of lane `lane` in row y (x0 = first node): pull, moments,
+// collision or wall closure, optional Eq. 6 accumulation and probe sampling, store.
+// step_time() = global index of the step being produced (called only when a probe sits in this
+// segment).
+template <typename S, bool SHIFTED, bool REDUCE, int V, int HINT, typename Probes, typename TimeFn>
+__device__ __forceinline__ void step_row(const S* __restrict__ src, S* __restrict__ dst,
+                                         const CavityView<typename St<S>::C>& cv, int lane, int x0,
+                                         int y, typename St<S>::C* snap, const Probes& probes,
+                                         TimeFn step_time,
+                                         typename St<S>::C& acc_drho, typename St<S>::C& acc_num,
+                                         typename St<S>::C& acc_den) {
+    using C = typename St<S>::C;
+    const int nx = cv.nx, ny = cv.ny;
+    const long long pitch = cv.pitch, plane = cv.plane;
+    const C omega = cv.omega;
+    const C keep = C(1.0) - omega;  // 1 - 1/tau (wall nodes)
+    C f[9][V];
+    pull_segment<S, SHIFTED, V, HINT>(src, lane, x0, y, nx, ny, pitch, plane, f);
+    C sx[V], sy[V];
+    if constexpr (REDUCE) {
+        cload<C, V, HINT == 2>(snap + (long long)y * pitch + x0, sx);
+        cload<C, V, HINT == 2>(snap + plane + (long long)y * pitch + x0, sy);
+    }
+    // observing points on this row segment (Sec. 3.3)
+    unsigned pmask = 0;
+    for (int q = 0; q < probes.n(); ++q)
+        if (probes.py(q) == y && probes.px(q) >= x0 && probes.px(q) < x0 + V) pmask |= 1u << q;
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        const int x = x0 + i;
+        C g[9];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) g[j] = f[j][i];
+        const C drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+        const C rho = C(1.0) + drho;
+        const C jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+        const C jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
+        const C inv = rcp<C>(rho);
+        const C ux = jx * inv, uy = jy * inv;
+        C e[9];
+        geq9<C>(drho, rho, ux, uy, e);
+        const bool wall = (y == 0) | (y == ny - 1) | (x == 0) | (x >= nx - 1);
+        C uox = ux, uoy = uy;
+        if (wall) {
+            const bool lid = (y == ny - 1) && (cv.corner_moving || (x > 0 && x < nx - 1));
+            uox = lid ? cv.Ulid : C(0.0);
+            uoy = C(0.0);
+            C ew[9];
+            geq9<C>(drho, rho, uox, uoy, ew);
+#pragma unroll
+            for (int j = 0; j < 9; ++j) f[j][i] = ew[j] + keep * (g[j] - e[j]);
+        } else {
+            // BGK as an increment d_j = (f^eq_j - f_j)/tau added to the pulled value.  The
+            // increment must carry no momentum; in FP32 the rounding of f^eq breaks that by a
+            // few ulps in the same direction every step, so the x and y momentum of d is
+            // removed from the (1,3) and (2,4) pairs (a rounding-level change).
+            C d[9];
+#pragma unroll
+            for (int j = 0; j < 9; ++j) d[j] = omega * (e[j] - g[j]);
+            if constexpr (sizeof(C) == 4) {
+                const C mx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+                const C my = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+                d[1] -= C(0.5) * mx;
+                d[3] += C(0.5) * mx;
+                d[2] -= C(0.5) * my;
+                d[4] += C(0.5) * my;
+            }
+#pragma unroll
+            for (int j = 0; j < 9; ++j) f[j][i] = g[j] + d[j];
+        }
+        if (x >= nx) {
+#pragma unroll
+            for (int j = 0; j < 9; ++j) f[j][i] = C(0.0);
+        }
+        if constexpr (REDUCE) {
+            if (x < nx) {
+                const C dx = uox - sx[i], dy = uoy - sy[i];  // exact when close (Sterbenz)
+                acc_drho += drho;
+                acc_num += dx * dx + dy * dy;
+                acc_den += sx[i] * sx[i] + sy[i] * sy[i];
+            }
+            sx[i] = x < nx ? uox : C(0);
+            sy[i] = x < nx ? uoy : C(0);
+        }
+        if (pmask) {
+            for (int q = 0; q < probes.n(); ++q) {
+                if (((pmask >> q) & 1u) && probes.px(q) == x) {
+                    const long long t = step_time();
+                    const int ev = probes.every(q);
+                    if (t % ev == 0) {
+                        long long k = t / ev - probes.start(q) / ev - 1;
+                        if (k >= 0) {
+                            k %= probes.cap(q);
+                            probes.series(q)[2 * k] = double(uox);
+                            probes.series(q)[2 * k + 1] = double(uoy);
+                        }
+                    }
+                }
+            }
+        }
+    }
+
+    S* pd = dst + (long long)y * pitch + x0;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        if constexpr (!SHIFTED) {
+#pragma unroll
+            for (int i = 0; i < V; ++i) f[j][i] += C(wd(j));
+        }
+        vstore_n<S, V>(pd + j * plane, f[j]);
+    }
+    if constexpr (REDUCE) {
+        cstore<C, V>(snap + (long long)y * pitch + x0, sx);
+        cstore<C, V>(snap + plane + (long long)y * pitch + x0, sy);
+    }
+}
+
+// Sum of three per-thread values over the block's warps into partials[3*block .. 3*block+2].
+template <int BY, typename C>
+__device__ __forceinline__ void block_partials(C a0, C a1, C a2, double* partials, long long block) {
+    __shared__ double red[3][BY];
+    const double s0 = warp_sum(double(a0));
+    const double s1 = warp_sum(double(a1));
+    const double s2 = warp_sum(double(a2));
+    if (threadIdx.x == 0) {
+        red[0][threadIdx.y] = s0;
+        red[1][threadIdx.y] = s1;
+        red[2][threadIdx.y] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.y == 0 && threadIdx.x < 3) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < BY; ++w) s += red[threadIdx.x][w];
+        partials[3 * block + threadIdx.x] = s;
     }
 }
 
@@ -199,140 +394,26 @@ __global__ void __launch_bounds__(32 * BY) k_step(const StepArgs a) {
     const int lane = threadIdx.x;
     const int x0 = (blockIdx.x * 32 + lane) * V;
     const int yb = (blockIdx.y * BY + threadIdx.y) * R;
-    const int nx = a.nx, ny = a.ny;
-    const long long pitch = a.pitch, plane = a.plane;
+    CavityView<C> cv;
+    cv.nx = a.nx;
+    cv.ny = a.ny;
+    cv.pitch = a.pitch;
+    cv.plane = a.plane;
+    cv.omega = sizeof(C) == 4 ? C(a.omega_f) : C(a.omega);
+    cv.Ulid = sizeof(C) == 4 ? C(a.U_f) : C(a.U);
+    cv.corner_moving = a.corner_moving;
     const S* __restrict__ src = static_cast<const S*>(a.src);
     S* __restrict__ dst = static_cast<S*>(a.dst);
-    const C omega = C(a.omega);
-    const C keep = C(1.0) - omega;  // 1 - 1/tau (wall nodes)
-    const C Ulid = C(a.U);
-
     C acc_drho = C(0), acc_num = C(0), acc_den = C(0);
-
 #pragma unroll 1
     for (int r = 0; r < R; ++r) {
         const int y = yb + r;
-        if (y >= ny) break;  // uniform across the warp
-        C f[9][V];
-        pull_segment<S, SHIFTED, V, HINT>(src, lane, x0, y, nx, ny, pitch, plane, f);
-        C* snap = static_cast<C*>(a.snap);
-        C sx[V], sy[V];
-        if constexpr (REDUCE) {
-            cload<C, V>(snap + (long long)y * pitch + x0, sx);
-            cload<C, V>(snap + plane + (long long)y * pitch + x0, sy);
-        }
-        // observing points on this row segment (Sec. 3.3)
-        unsigned pmask = 0;
-        for (int q = 0; q < a.probes.n; ++q)
-            if (a.probes.py[q] == y && a.probes.px[q] >= x0 && a.probes.px[q] < x0 + V) pmask |= 1u << q;
-#pragma unroll
-        for (int i = 0; i < V; ++i) {
-            const int x = x0 + i;
-            C g[9];
-#pragma unroll
-            for (int j = 0; j < 9; ++j) g[j] = f[j][i];
-            const C drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
-            const C rho = C(1.0) + drho;
-            const C jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
-            const C jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
-            const C inv = rcp<C>(rho);
-            const C ux = jx * inv, uy = jy * inv;
-            C e[9];
-            geq9<C>(drho, rho, ux, uy, e);
-            const bool wall = (y == 0) | (y == ny - 1) | (x == 0) | (x >= nx - 1);
-            C uox = ux, uoy = uy;
-            if (wall) {
-                const bool lid = (y == ny - 1) && (a.corner_moving || (x > 0 && x < nx - 1));
-                uox = lid ? Ulid : C(0.0);
-                uoy = C(0.0);
-                C ew[9];
-                geq9<C>(drho, rho, uox, uoy, ew);
-#pragma unroll
-                for (int j = 0; j < 9; ++j) f[j][i] = ew[j] + keep * (g[j] - e[j]);
-            } else {
-                // BGK as an increment d_j = (f^eq_j - f_j)/tau added to the pulled value.  The
-                // increment must carry no momentum; in FP32 the rounding of f^eq breaks that by a
-                // few ulps in the same direction every step, so the x and y momentum of d is
-                // removed from the (1,3) and (2,4) pairs (a rounding-level change).
-                C d[9];
-#pragma unroll
-                for (int j = 0; j < 9; ++j) d[j] = omega * (e[j] - g[j]);
-                if constexpr (sizeof(C) == 4) {
-                    const C mx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
-                    const C my = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
-                    d[1] -= C(0.5) * mx;
-                    d[3] += C(0.5) * mx;
-                    d[2] -= C(0.5) * my;
-                    d[4] += C(0.5) * my;
-                }
-#pragma unroll
-                for (int j = 0; j < 9; ++j) f[j][i] = g[j] + d[j];
-            }
-            if (x >= nx) {
-#pragma unroll
-                for (int j = 0; j < 9; ++j) f[j][i] = C(0.0);
-            }
-            if constexpr (REDUCE) {
-                if (x < nx) {
-                    const C dx = uox - sx[i], dy = uoy - sy[i];  // exact when close (Sterbenz)
-                    acc_drho += drho;
-                    acc_num += dx * dx + dy * dy;
-                    acc_den += sx[i] * sx[i] + sy[i] * sy[i];
-                }
-                sx[i] = x < nx ? uox : C(0);
-                sy[i] = x < nx ? uoy : C(0);
-            }
-            if (pmask) {
-                for (int q = 0; q < a.probes.n; ++q) {
-                    if (((pmask >> q) & 1u) && a.probes.px[q] == x) {
-                        const long long t = a.state->base + a.s + 1;
-                        const int ev = a.probes.every[q];
-                        if (t % ev == 0) {
-                            long long k = t / ev - a.probes.start[q] / ev - 1;
-                            if (k >= 0) {
-                                k %= a.probes.cap[q];
-                                a.probes.series[q][2 * k] = double(uox);
-                                a.probes.series[q][2 * k + 1] = double(uoy);
-                            }
-                        }
-                    }
-                }
-            }
-        }
-
-        S* pd = dst + (long long)y * pitch + x0;
-#pragma unroll
-        for (int j = 0; j < 9; ++j) {
-            if constexpr (!SHIFTED) {
-#pragma unroll
-                for (int i = 0; i < V; ++i) f[j][i] += C(wd(j));
-            }
-            vstore_n<S, V>(pd + j * plane, f[j]);
-        }
-        if constexpr (REDUCE) {
-            cstore<C, V>(snap + (long long)y * pitch + x0, sx);
-            cstore<C, V>(snap + plane + (long long)y * pitch + x0, sy);
-        }
+        if (y >= a.ny) break;  // uniform across the warp
+        step_row<S, SHIFTED, REDUCE, V, HINT>(
+            src, dst, cv, lane, x0, y, static_cast<C*>(a.snap), ProbeList{a.probes},
+            [&]() { return a.state->base + a.s + 1; }, acc_drho, acc_num, acc_den);
     }
-
-    if constexpr (REDUCE) {
-        __shared__ double red[3][BY];
-        const double s0 = warp_sum(double(acc_drho));
-        const double s1 = warp_sum(double(acc_num));
-        const double s2 = warp_sum(double(acc_den));
-        if (lane == 0) {
-            red[0][threadIdx.y] = s0;
-            red[1][threadIdx.y] = s1;
-            red[2][threadIdx.y] = s2;
-        }
-        __syncthreads();
-        if (threadIdx.y == 0 && lane < 3) {
-            double s = 0.0;
-#pragma unroll
-            for (int w = 0; w < BY; ++w) s += red[lane][w];
-            a.partials[3ll * (blockIdx.y * gridDim.x + blockIdx.x) + lane] = s;
-        }
-    }
+    if constexpr (REDUCE) block_partials<BY>(acc_drho, acc_num, acc_den, a.partials, (long long)blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // Launch shape (nodes per lane V, rows per thread R, warps per block BY, load hint).  Every shape

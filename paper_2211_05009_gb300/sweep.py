@@ -1,0 +1,122 @@
+"""Re x Ar sweep of lid-driven rectangular cavities (Sec. 3.3, Fig. 17; Table 3 periods):
+batched persistent run against one-cavity-at-a-time runs, time to steady state at equal residual.
+
+  python -m paper_2211_05009_gb300.sweep --nx 500 --tol 1e-9 --max-steps 1000000 --sequential
+
+Cavities: nx x round(nx Ar) nodes, U = 0.1 (lattice units), Re = U nx / nu.  Each runs until its
+Eq. 6 residual is below tol or max-steps steps were taken.  The batched arm steps all cavities in
+one persistent launch per 100 steps and retires converged ones; the sequential arm runs the same
+cavities one after another through the single-cavity API (lbm_run_to_residual).  Each cavity
+records u_x, u_y at the Sec. 3.3 observing point every `probe-every` steps, and its flow state is
+classified from that series (analysis.classify).  Prints one JSON document.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+import torch
+
+from . import binding as B
+from .analysis import classify, observing_point
+from .build import build
+
+RE_DEFAULT = "4000,5000,6000,7000,8000"
+AR_DEFAULT = "0.4,0.6,0.8,1.0,1.2,1.4,1.6,1.8,2.0"
+
+
+def cavity_list(nx, res, ars, U):
+    cases = []
+    for ar in ars:
+        for re in res:
+            cases.append({"Re": re, "Ar": ar, "nx": nx, "ny": int(round(nx * ar)), "U": U})
+    return cases
+
+
+def run_batched(cases, dtype, tol, max_steps, every, cap):
+    st = torch.cuda.current_stream()
+    b = B.lbm_batch_create([c["nx"] for c in cases], [c["ny"] for c in cases], [c["Re"] for c in cases],
+                           [c["U"] for c in cases], dtype)
+    try:
+        B.lbm_batch_set_stream(b, st.cuda_stream)
+        series = torch.zeros((len(cases), cap, 2), dtype=torch.float64, device="cuda")
+        pts = [observing_point(c["Ar"]) for c in cases]
+        B.lbm_batch_probe(b, [p[0] for p in pts], [p[1] for p in pts], every, series, cap)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, done = B.lbm_batch_run_to_residual(b, len(cases), tol, max_steps)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        r, status = B.lbm_batch_residual(b, len(cases))
+        out = []
+        ser = series.cpu().numpy()
+        for i, c in enumerate(cases):
+            n = int(done[i]) // every
+            k = min(n, cap)
+            ux = np.roll(ser[i, :, 0], -(n % cap))[-k:] if n > cap else ser[i, :k, 0]
+            fs = classify(ux, every, c["U"], c["nx"], converged=bool(status[i] == 1)) if k >= 8 else None
+            psi_min, xc, yc = B.lbm_batch_stream_function(b, i)
+            out.append({**c, "steps": int(done[i]), "residual": float(r[i]), "status": int(status[i]),
+                        "state": fs.state if fs else None,
+                        "period_steps": fs.period_steps if fs else None,
+                        "period_convective": fs.period_convective if fs else None,
+                        "psi_min": psi_min, "xc": xc, "yc": yc})
+        lu = sum(c["nx"] * c["ny"] * o["steps"] for c, o in zip(cases, out))
+        return {"wall_s": wall, "lattice_updates": lu, "glups": lu / wall / 1e9,
+                "all_converged": rc == B.LBM_OK, "cavities": out}
+    finally:
+        B.lbm_batch_destroy(b)
+
+
+def run_sequential(cases, dtype, tol, max_steps):
+    st = torch.cuda.current_stream()
+    out, total, lu = [], 0.0, 0
+    for c in cases:
+        ctx = B.lbm_create(c["nx"], c["ny"], c["Re"], c["U"], dtype)
+        try:
+            B.lbm_set_stream(ctx, st.cuda_stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, done = B.lbm_run_to_residual(ctx, tol, max_steps)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            total += wall
+            lu += c["nx"] * c["ny"] * done
+            out.append({"Re": c["Re"], "Ar": c["Ar"], "steps": done, "wall_s": wall,
+                        "residual": B.lbm_residual(ctx) if done >= 100 else None,
+                        "converged": rc == B.LBM_OK})
+        finally:
+            B.lbm_destroy(ctx)
+    return {"wall_s": total, "lattice_updates": lu, "glups": lu / total / 1e9, "cavities": out}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--nx", type=int, default=500)
+    ap.add_argument("--re", default=RE_DEFAULT)
+    ap.add_argument("--ar", default=AR_DEFAULT)
+    ap.add_argument("--u", type=float, default=0.1)
+    ap.add_argument("--dtype", default="f32s")
+    ap.add_argument("--tol", type=float, default=1e-9)
+    ap.add_argument("--max-steps", type=int, default=1_000_000)
+    ap.add_argument("--probe-every", type=int, default=100)
+    ap.add_argument("--sequential", action="store_true", help="also run the one-at-a-time arm")
+    a = ap.parse_args(argv)
+    build()
+    res = [float(v) for v in a.re.split(",")]
+    ars = [float(v) for v in a.ar.split(",")]
+    cases = cavity_list(a.nx, res, ars, a.u)
+    cap = max(8, a.max_steps // a.probe_every)
+    doc = {"nx": a.nx, "U": a.u, "dtype": a.dtype, "tol": a.tol, "max_steps": a.max_steps,
+           "n_cavities": len(cases), "nodes": sum(c["nx"] * c["ny"] for c in cases)}
+    doc["batched"] = run_batched(cases, a.dtype, a.tol, a.max_steps, a.probe_every, cap)
+    if a.sequential:
+        doc["sequential"] = run_sequential(cases, a.dtype, a.tol, a.max_steps)
+        doc["speedup_time_to_steady"] = doc["sequential"]["wall_s"] / doc["batched"]["wall_s"]
+    print(json.dumps(doc), flush=True)
+
+
+if __name__ == "__main__":
+    main()

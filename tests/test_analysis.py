@@ -1,0 +1,45 @@
+"""The flow-state rule of paper_2211_05009_gb300.analysis on signals whose state is known."""
+import numpy as np
+
+from paper_2211_05009_gb300.analysis import classify, observing_point
+
+
+def test_constant_signal_is_steady():
+    s = classify(np.full(400, 0.0123), every=100, U=0.1, nx=500)
+    assert s.state == "steady" and s.period_steps is None
+
+
+def test_converged_run_is_steady():
+    s = classify(np.sin(np.arange(400)), every=100, U=0.1, nx=500, converged=True)
+    assert s.state == "steady"
+
+
+def test_sinusoid_is_periodic_with_its_period():
+    every, period = 100, 3137.0  # steps
+    t = np.arange(4000) * every
+    ux = 0.01 + 1e-3 * np.sin(2 * np.pi * t / period) + 3e-4 * np.sin(4 * np.pi * t / period + 1.0)
+    s = classify(ux, every=every, U=0.1, nx=500)
+    assert s.state == "periodic"
+    assert abs(s.period_steps - period) < 0.02 * period
+    assert abs(s.period_convective - period * 0.1 / 500) < 0.02 * period * 0.1 / 500
+
+
+def test_incommensurate_and_noisy_signal_is_aperiodic():
+    rng = np.random.default_rng(0)
+    t = np.arange(4000, dtype=float)
+    ux = np.sin(t / 7.3) + np.sin(t / (7.3 * np.sqrt(2))) + 0.5 * rng.normal(size=t.size)
+    assert classify(ux, every=100, U=0.1, nx=500).state == "aperiodic"
+
+
+def test_logistic_map_chaos_is_aperiodic():
+    x = np.empty(4000)
+    x[0] = 0.3
+    for i in range(1, len(x)):
+        x[i] = 3.9 * x[i - 1] * (1 - x[i - 1])
+    assert classify(1e-3 * x, every=100, U=0.1, nx=500).state == "aperiodic"
+
+
+def test_observing_points_of_sec_3_3():
+    assert observing_point(0.4) == (0.5, 0.2)
+    assert observing_point(0.5) == observing_point(0.6) == (0.5, 0.3)
+    assert observing_point(1.2) == (0.5, 0.5)
