@@ -5,7 +5,9 @@
 // Work decomposition: every cavity is cut into items of one warp-wide column strip (32*V nodes)
 // by R rows; items of all active cavities are numbered consecutively and the warps of the grid
 // take them round-robin, so small and large cavities share the GPU.  A launch runs up to one
-// checkpoint interval (100 steps); steps are separated by a grid barrier.  The launch is
+// checkpoint interval (the plain steps, then the checkpoint step as a second launch of the
+// REDUCE variant, which keeps the plain variant's register budget small); steps are separated by
+// a grid barrier.  The launch is
 // cooperative (all blocks resident) and every barrier wait is bounded by a clock limit: when it
 // runs out the kernel sets an error word and returns, and the host reports LBM_ETIMEOUT.
 // At each checkpoint (Sec. 2.2 iii) every cavity gets its own Eq. 6 residual and mass (fixed-order
@@ -30,7 +32,7 @@
 namespace lbm {
 
 constexpr int kBatchThreads = 128;
-constexpr int kBatchR = 4;  // rows per item
+constexpr int kBatchR = 2;  // rows per item
 
 struct BatchCav {
     long long off;       // population offset (storage elements) in each pool
@@ -108,8 +110,10 @@ __device__ __forceinline__ bool grid_barrier(BatchState* st, long long limit) {
     return ok_sh != 0;
 }
 
-template <typename S, bool SHIFTED, int V>
-__global__ void __launch_bounds__(kBatchThreads, 4) k_batch(const BatchArgs a) {
+// REDUCE = false: a.nsteps plain steps (none of them a checkpoint step).  REDUCE = true: exactly
+// one step, the checkpoint step, followed by the per-cavity reduction and the compaction.
+template <typename S, bool SHIFTED, int V, bool REDUCE>
+__global__ void __launch_bounds__(kBatchThreads, 5) k_batch(const BatchArgs a) {
     using C = typename St<S>::C;
     __shared__ int s_active[LBM_BATCH_MAX];
     __shared__ int s_prefix[LBM_BATCH_MAX + 1];
@@ -124,7 +128,7 @@ __global__ void __launch_bounds__(kBatchThreads, 4) k_batch(const BatchArgs a) {
 
     for (int s = 0; s < a.nsteps; ++s) {
         const long long step = step0 + s;
-        const bool reduce = (step + 1) % kInterval == 0;
+        constexpr bool reduce = REDUCE;
         // the active list (changes only at checkpoints, behind barriers)
         if (threadIdx.x == 0) s_n = __ldcg(&st->n_active);
         __syncthreads();
@@ -167,17 +171,14 @@ __global__ void __launch_bounds__(kBatchThreads, 4) k_batch(const BatchArgs a) {
             C* snap = static_cast<C*>(a.snap) + cd.snap_off;
             const int x0 = (strip * 32 + lane) * V;
             C a0 = C(0), a1 = C(0), a2 = C(0);
+#pragma unroll 1
             for (int r = 0; r < kBatchR; ++r) {
                 const int y = rg * kBatchR + r;
                 if (y >= cd.ny) break;
-                if (reduce)
-                    step_row<S, SHIFTED, true, V, 2>(src, dst, cv, lane, x0, y, snap, pr,
-                                                     [step]() { return step + 1; }, a0, a1, a2);
-                else
-                    step_row<S, SHIFTED, false, V, 2>(src, dst, cv, lane, x0, y, snap, pr,
-                                                      [step]() { return step + 1; }, a0, a1, a2);
+                step_row<S, SHIFTED, REDUCE, V, 2>(src, dst, cv, lane, x0, y, snap, pr,
+                                                   [step]() { return step + 1; }, a0, a1, a2);
             }
-            if (reduce) {
+            if constexpr (REDUCE) {
                 const double p0 = warp_sum(double(a0)), p1 = warp_sum(double(a1)), p2 = warp_sum(double(a2));
                 if (lane == 0) {
                     double* p = a.partials + 3ll * (cd.item0 + local);
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(kBatchThreads, 4) k_batch(const BatchArgs a) {
         }
         if (a.absent_block == (int)blockIdx.x && s == 0) return;  // test hook: never arrives
         if (!grid_barrier(st, a.spin_limit)) return;
-        if (!reduce) continue;
+        if constexpr (!REDUCE) continue;
 
         // checkpoint: per-cavity Eq. 6 and mass, in a fixed order
         __shared__ double red[3][kBatchThreads];
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(kBatchThreads, 4) k_batch(const BatchArgs a) {
 }
 
 template <typename S, bool SHIFTED>
-static cudaError_t launch_batch_t(const BatchArgs& a, int blocks, cudaStream_t st) {
+static cudaError_t launch_batch_t(const BatchArgs& a, bool reduce, int blocks, cudaStream_t st) {
     constexpr int V = sizeof(S) == 8 ? 2 : 4;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(blocks);
@@ -258,17 +259,19 @@ static cudaError_t launch_batch_t(const BatchArgs& a, int blocks, cudaStream_t s
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_batch<S, SHIFTED, V>, a);
+    if (reduce) return cudaLaunchKernelEx(&cfg, k_batch<S, SHIFTED, V, true>, a);
+    return cudaLaunchKernelEx(&cfg, k_batch<S, SHIFTED, V, false>, a);
 }
 
 template <typename S, bool SHIFTED>
 static int batch_blocks_t() {
     constexpr int V = sizeof(S) == 8 ? 2 : 4;
-    int dev = 0, sms = 0, per = 0;
+    int dev = 0, sms = 0, p0 = 0, p1 = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<S, SHIFTED, V>, kBatchThreads, 0) != cudaSuccess) return 0;
-    return per * sms;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p0, k_batch<S, SHIFTED, V, false>, kBatchThreads, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, k_batch<S, SHIFTED, V, true>, kBatchThreads, 0) != cudaSuccess) return 0;
+    return (p0 < p1 ? p0 : p1) * sms;  // one grid size that fits both variants
 }
 
 #define LBM_BATCH_DISPATCH(dtype, CALL)                                              \
@@ -281,8 +284,8 @@ static int batch_blocks_t() {
         default: break;                                                              \
     }
 
-static cudaError_t launch_batch(int dtype, const BatchArgs& a, int blocks, cudaStream_t st) {
-    LBM_BATCH_DISPATCH(dtype, return (launch_batch_t<S, SH>(a, blocks, st)));
+static cudaError_t launch_batch(int dtype, const BatchArgs& a, bool reduce, int blocks, cudaStream_t st) {
+    LBM_BATCH_DISPATCH(dtype, return (launch_batch_t<S, SH>(a, reduce, blocks, st)));
     return cudaErrorInvalidValue;
 }
 
@@ -391,8 +394,20 @@ struct lbm_batch {
             a.max_step = max_step;
             a.spin_limit = (long long)(spin_limit_s * clock_khz * 1000.0);
             a.absent_block = absent_block;
-            rc = cuda(launch_batch(dtype, a, blocks, stream), "batch kernel launch");
-            if (rc) return rc;
+            // plain steps first; a chunk that ends on a checkpoint ends with the REDUCE launch
+            const bool ends_on_checkpoint = (step + chunk) % kInterval == 0;
+            const long long plain = ends_on_checkpoint ? chunk - 1 : chunk;
+            if (plain > 0) {
+                a.nsteps = (int)plain;
+                rc = cuda(launch_batch(dtype, a, false, blocks, stream), "batch kernel launch");
+                if (rc) return rc;
+                a.absent_block = -1;
+            }
+            if (ends_on_checkpoint) {
+                a.nsteps = 1;
+                rc = cuda(launch_batch(dtype, a, true, blocks, stream), "batch checkpoint launch");
+                if (rc) return rc;
+            }
             absent_block = -1;
             step += chunk;
             n -= chunk;

