@@ -32,6 +32,7 @@
 namespace lbm {
 
 constexpr int kBatchThreads = 128;
+static_assert((kBatchThreads & (kBatchThreads - 1)) == 0, "tree reductions assume a power of two");
 constexpr int kBatchR = 2;  // rows per item
 
 struct BatchCav {
