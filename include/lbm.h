@@ -266,6 +266,11 @@ int lbm_batch_get_populations(lbm_batch *b, int i, double *f);
 int lbm_batch_stream_function(lbm_batch *b, int i, double *psi, double *psi_min, double *xc,
                               double *yc);
 
+/* Replace cavity i's state by f = f^eq(rho, u) from DEVICE [ny_i][nx_i] FP64 fields (a warm
+ * start); its Eq. 6 snapshot becomes u.  Only for an active cavity while the batch sits on a
+ * checkpoint boundary (step multiple of 100, e.g. right after lbm_batch_create).  Synchronising. */
+int lbm_batch_set_moments(lbm_batch *b, int i, const double *rho, const double *ux, const double *uy);
+
 /* One observing point per cavity at (x[i], y[i]) (width units, as lbm_probe); after every step
  * t with t % every == 0 cavity i writes (u_x, u_y) to dev_series[2 (i cap + k)], k = sample
  * number mod cap.  dev_series: caller-owned DEVICE buffer of 2 n cap doubles. */
@@ -279,6 +284,63 @@ int lbm_batch_info(lbm_batch *b, int i, lbm_info *info);
  * the next launch leave before its first barrier -- a fault-injection hook for testing the
  * timeout path (the other blocks' waits run out and the call returns LBM_ETIMEOUT). */
 int lbm_batch_set_barrier_limit(lbm_batch *b, double seconds, int absent_block);
+
+/* ------------------------------------------------------------------ learned warm start */
+
+/* Not in the paper: a convolutional encoder-decoder that predicts an initial fine field for the
+ * solver from (Re, Ar, a coarse field), to cut the steps to the Eq. 6 steady state; the plain run
+ * from rest remains the fallback and the judge.  Architecture: 5 levels of two 3x3 convolutions
+ * (widths w, 2w, 4w, 8w, 8w; leaky ReLU 0.1), 2x2 average pooling down, nearest x2 up with
+ * skip concatenation, a 3x3 output head.  Input tensor [7][H][W] FP32 (see lbm_warm_input),
+ * output [3][H][W]: corrections to input channels 0..2.  All convolutions run on BF16 tensor
+ * cores with FP32 accumulation; master weights and Adam state are FP32.  H, W: multiples of 16
+ * with (H/16)(W/16) a multiple of 8.  Tensor arguments are DEVICE pointers. */
+#define LBM_WARM_RHO_SCALE 100.0f /* channel 0 holds (rho - 1) * LBM_WARM_RHO_SCALE */
+typedef struct lbm_net lbm_net;
+
+/* He-uniform initial weights from a seeded generator; biases zero. */
+int lbm_net_create(int width, unsigned long long seed, lbm_net **out);
+void lbm_net_destroy(lbm_net *n);
+const char *lbm_net_last_error(const lbm_net *n);
+int lbm_net_set_stream(lbm_net *n, void *cuda_stream);
+long lbm_net_param_count(const lbm_net *n);
+/* Flat FP32 parameter / gradient vectors (host or device buffers of lbm_net_param_count floats).
+ * Order: per convolution (the 10 encoder, 8 decoder, 1 head convolutions in graph order) its
+ * weights [co][ci][3][3] then its biases [co]. */
+int lbm_net_get_params(lbm_net *n, float *p);
+int lbm_net_set_params(lbm_net *n, const float *p);
+int lbm_net_get_grads(lbm_net *n, float *g);
+int lbm_net_zero_grads(lbm_net *n);
+/* out[3][H][W] = network(in[7][H][W]).  Asynchronous. */
+int lbm_net_forward(lbm_net *n, const float *in, int H, int W, float *out);
+/* Forward, loss = mean over masked pixels and 3 channels of (base + out - target)^2, backward:
+ * gradients are ADDED to the accumulated gradient (lbm_net_zero_grads clears it).  mask [H][W]
+ * is 0/1; base, target [3][H][W].  *loss (host, may be NULL).  Synchronising. */
+int lbm_net_backward(lbm_net *n, const float *in, const float *base, const float *target,
+                     const float *mask, int H, int W, double *loss);
+/* One Adam step on the accumulated gradient times grad_scale (e.g. 1/batch). */
+int lbm_net_adam_step(lbm_net *n, float lr, float beta1, float beta2, float eps, float grad_scale);
+int lbm_net_save(lbm_net *n, const char *path);
+int lbm_net_load(lbm_net *n, const char *path);
+
+/* Network input for a fine nx x ny cavity (rows padded to H >= ny) from a coarse nxc x nyc
+ * solution (DEVICE [nyc][nxc] FP64 rho, ux, uy, e.g. lbm_moments of a coarse run): bilinear image
+ * of (rho - 1) * LBM_WARM_RHO_SCALE, ux / U, uy / U on the fine nodes, Re / 4000, Ar / 2, the wall
+ * mask and the valid-row mask.  in: DEVICE [7][H][nx] FP32.  Asynchronous. */
+int lbm_warm_input(const double *rho_c, const double *ux_c, const double *uy_c, int nxc, int nyc,
+                   double Re, double Ar, double U, int nx, int ny, int H, float *in, void *stream);
+/* Fine fields (DEVICE [ny][nx] FP64) from the input and the network output: base + correction,
+ * unscaled -- ready for lbm_set_moments.  Asynchronous. */
+int lbm_warm_output(const float *in, const float *out, int nx, int ny, int H, double U, double *rho,
+                    double *ux, double *uy, void *stream);
+
+/* The network's tensor-core product, exposed for tests and reuse: C[M][N] (op)= sum_k A[M][K]
+ * B[N][K] with A, B bfloat16 (DEVICE, row-major, K contiguous; K, lda, ldb multiples of 8, 16-byte
+ * aligned) and C FP32 (DEVICE, ldc).  op: 0 store, 1 accumulate, 2 atomic add (required when
+ * split_k > 1: K is split across split_k blocks whose partial products are added atomically).
+ * Asynchronous.  LBM_EINVAL for sizes or alignments it does not support. */
+int lbm_nn_gemm_bf16(int M, int N, int K, const void *A, int lda, const void *B, int ldb, float *C,
+                     int ldc, int op, int split_k, void *stream);
 
 /* ------------------------------------------------------------------ checkpoint */
 

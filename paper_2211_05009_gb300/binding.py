@@ -84,8 +84,26 @@ _SIGS = [
     ("lbm_batch_get_populations", _I, [_P, _I, _P]),
     ("lbm_batch_stream_function", _I, [_P, _I, _P, _DP, _DP, _DP]),
     ("lbm_batch_probe", _I, [_P, _P, _P, _I, _P, _L]),
+    ("lbm_batch_set_moments", _I, [_P, _I, _P, _P, _P]),
     ("lbm_batch_info", _I, [_P, _I, ctypes.POINTER(lbm_info)]),
     ("lbm_batch_set_barrier_limit", _I, [_P, _D, _I]),
+    ("lbm_net_create", _I, [_I, ctypes.c_ulonglong, ctypes.POINTER(_P)]),
+    ("lbm_net_destroy", None, [_P]),
+    ("lbm_net_last_error", ctypes.c_char_p, [_P]),
+    ("lbm_net_set_stream", _I, [_P, _P]),
+    ("lbm_net_param_count", _L, [_P]),
+    ("lbm_net_get_params", _I, [_P, _P]),
+    ("lbm_net_set_params", _I, [_P, _P]),
+    ("lbm_net_get_grads", _I, [_P, _P]),
+    ("lbm_net_zero_grads", _I, [_P]),
+    ("lbm_net_forward", _I, [_P, _P, _I, _I, _P]),
+    ("lbm_net_backward", _I, [_P, _P, _P, _P, _P, _I, _I, _DP]),
+    ("lbm_net_adam_step", _I, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+    ("lbm_net_save", _I, [_P, ctypes.c_char_p]),
+    ("lbm_net_load", _I, [_P, ctypes.c_char_p]),
+    ("lbm_warm_input", _I, [_P, _P, _P, _I, _I, _D, _D, _D, _I, _I, _I, _P, _P]),
+    ("lbm_warm_output", _I, [_P, _P, _I, _I, _I, _D, _P, _P, _P, _P]),
+    ("lbm_nn_gemm_bf16", _I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _I, _P]),
     ("lbm_save", _I, [_P, ctypes.c_char_p]),
     ("lbm_load", _I, [_P, ctypes.c_char_p]),
 ]
@@ -344,6 +362,10 @@ def lbm_batch_stream_function(b, i: int, psi=None):
     return vmin.value, xc.value, yc.value
 
 
+def lbm_batch_set_moments(b, i: int, rho, ux, uy) -> None:
+    _bcheck(b, library().lbm_batch_set_moments(b, i, _ptr(rho), _ptr(ux), _ptr(uy)))
+
+
 def lbm_batch_probe(b, x, y, every: int, dev_series, cap: int) -> None:
     ax = np.ascontiguousarray(x, dtype=np.float64)
     ay = np.ascontiguousarray(y, dtype=np.float64)
@@ -358,3 +380,96 @@ def lbm_batch_info(b, i: int) -> lbm_info:
 
 def lbm_batch_set_barrier_limit(b, seconds: float, absent_block: int = -1) -> None:
     _bcheck(b, library().lbm_batch_set_barrier_limit(b, float(seconds), int(absent_block)))
+
+
+# ------------------------------------------------------------------ learned warm start
+LBM_WARM_RHO_SCALE = 100.0
+
+
+def _tptr(t):
+    """Device address of a torch tensor of any dtype (contiguous), or None."""
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    return t.data_ptr()
+
+
+def _ncheck(n, rc: int):
+    if rc != LBM_OK:
+        raise LBMError(rc, library().lbm_net_last_error(n).decode(errors="replace"))
+
+
+def lbm_net_create(width: int, seed: int = 0):
+    out = ctypes.c_void_p()
+    _ncheck(None, library().lbm_net_create(int(width), int(seed), ctypes.byref(out)))
+    return out.value
+
+
+def lbm_net_destroy(n) -> None:
+    library().lbm_net_destroy(n)
+
+
+def lbm_net_set_stream(n, stream_handle) -> None:
+    _ncheck(n, library().lbm_net_set_stream(n, stream_handle))
+
+
+def lbm_net_param_count(n) -> int:
+    return library().lbm_net_param_count(n)
+
+
+def lbm_net_get_params(n, p) -> None:
+    _ncheck(n, library().lbm_net_get_params(n, _tptr(p) if not isinstance(p, np.ndarray) else p.ctypes.data))
+
+
+def lbm_net_set_params(n, p) -> None:
+    _ncheck(n, library().lbm_net_set_params(n, _tptr(p) if not isinstance(p, np.ndarray) else p.ctypes.data))
+
+
+def lbm_net_get_grads(n, g) -> None:
+    _ncheck(n, library().lbm_net_get_grads(n, _tptr(g) if not isinstance(g, np.ndarray) else g.ctypes.data))
+
+
+def lbm_net_zero_grads(n) -> None:
+    _ncheck(n, library().lbm_net_zero_grads(n))
+
+
+def lbm_net_forward(n, inp, H: int, W: int, out) -> None:
+    _ncheck(n, library().lbm_net_forward(n, _tptr(inp), int(H), int(W), _tptr(out)))
+
+
+def lbm_net_backward(n, inp, base, target, mask, H: int, W: int) -> float:
+    loss = ctypes.c_double()
+    _ncheck(n, library().lbm_net_backward(n, _tptr(inp), _tptr(base), _tptr(target), _tptr(mask), int(H), int(W),
+                                          ctypes.byref(loss)))
+    return loss.value
+
+
+def lbm_net_adam_step(n, lr: float, beta1=0.9, beta2=0.999, eps=1e-8, grad_scale=1.0) -> None:
+    _ncheck(n, library().lbm_net_adam_step(n, lr, beta1, beta2, eps, grad_scale))
+
+
+def lbm_net_save(n, path: str) -> None:
+    _ncheck(n, library().lbm_net_save(n, path.encode()))
+
+
+def lbm_net_load(n, path: str) -> None:
+    _ncheck(n, library().lbm_net_load(n, path.encode()))
+
+
+def lbm_warm_input(rho_c, ux_c, uy_c, nxc, nyc, Re, Ar, U, nx, ny, H, inp, stream_handle=None) -> None:
+    rc = library().lbm_warm_input(_tptr(rho_c), _tptr(ux_c), _tptr(uy_c), nxc, nyc, float(Re), float(Ar), float(U),
+                                  nx, ny, H, _tptr(inp), stream_handle)
+    if rc != LBM_OK:
+        raise LBMError(rc, "lbm_warm_input")
+
+
+def lbm_warm_output(inp, out, nx, ny, H, U, rho, ux, uy, stream_handle=None) -> None:
+    rc = library().lbm_warm_output(_tptr(inp), _tptr(out), nx, ny, H, float(U), _tptr(rho), _tptr(ux), _tptr(uy),
+                                   stream_handle)
+    if rc != LBM_OK:
+        raise LBMError(rc, "lbm_warm_output")
+
+
+def lbm_nn_gemm_bf16(M, N, K, A, lda, B, ldb, C, ldc, op=0, split_k=1, stream_handle=None) -> int:
+    return library().lbm_nn_gemm_bf16(M, N, K, _tptr(A), lda, _tptr(B), ldb, _tptr(C), ldc, op, split_k, stream_handle)

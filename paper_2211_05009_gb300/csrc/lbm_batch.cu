@@ -725,3 +725,23 @@ extern "C" int lbm_batch_set_barrier_limit(lbm_batch* b, double seconds, int abs
     b->absent_block = absent_block;
     return LBM_OK;
 }
+
+extern "C" int lbm_batch_set_moments(lbm_batch* b, int i, const double* rho, const double* ux, const double* uy) {
+    if (!b || i < 0 || i >= b->n || !rho || !ux || !uy) return b ? b->fail(LBM_EINVAL, "bad arguments") : LBM_EINVAL;
+    int rc = b->pull_state();
+    if (rc) return rc;
+    for (const double* p : {rho, ux, uy}) {
+        cudaPointerAttributes at{};
+        cudaError_t e = cudaPointerGetAttributes(&at, p);
+        if (e != cudaSuccess) cudaGetLastError();
+        if (!(e == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)))
+            return b->fail(LBM_EINVAL, "lbm_batch_set_moments needs device buffers");
+    }
+    if (b->h_state->done_at[i] >= 0 || b->step % kInterval != 0)
+        return b->fail(LBM_EINVAL, "cavity retired, or the batch is not at a checkpoint boundary");
+    const BatchCav& c = b->cavs[i];
+    void* sp = (char*)b->snap + c.snap_off * arith_bytes(b->dtype);
+    rc = b->cuda(launch_set_moments(b->dtype, b->field(i), rho, ux, uy, sp, b->stream), "set_moments launch");
+    if (!rc) rc = b->sync();
+    return rc;
+}

@@ -1,0 +1,27 @@
+// lbm_nn_gemm.cuh -- BF16 tensor-core GEMM with FP32 accumulation for the warm-start network.
+//
+//   C[M][N] (op)= sum_k A[M][K] * B[N][K]      (both operands K-contiguous, "NT" form)
+//
+// One form serves every convolution product of the network (forward, data gradient, weight
+// gradient), with the operands laid out by the im2col kernels.  Block tile 64 x 64, K step 32,
+// 4 warps of 32 x 32; operands staged to shared memory with cp.async (16-byte chunks, zero-fill
+// outside the matrix), fragments loaded with ldmatrix, products by mma.sync m16n8k16 (BF16 in,
+// FP32 accumulate).  Split-K over gridDim.z adds partial products into C atomically.
+// Requirements: K, lda, ldb multiples of 8 (16-byte rows); pointers 16-byte aligned.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+namespace nn {
+
+enum GemmOp { kStore = 0, kAccumulate = 1, kAtomicAdd = 2 };
+
+cudaError_t gemm_bf16_nt(int M, int N, int K, const __nv_bfloat16* A, int lda,
+                         const __nv_bfloat16* B, int ldb, float* C, int ldc, GemmOp op,
+                         int split_k, cudaStream_t st);
+
+}  // namespace nn
+}  // namespace lbm

@@ -1,0 +1,208 @@
+"""Learned warm start for the cavity solver: data, training and evaluation.
+
+  python -m paper_2211_05009_gb300.warmstart --train 400 --test 200 --epochs 30 --out net.bin
+
+1. Draws (Re, Ar) with Re ~ U[100, 4000], Ar ~ U[0.4, 2.0] (training seed 0, test seed 1).
+2. Coarse solutions: every draw on 64 x round(64 Ar) nodes, run in one batch to its Eq. 6
+   tolerance or a step cap.  The coarse grid cannot resolve the highest Re (tau -> 1/2), so the
+   coarse run uses Re_c = min(Re, --coarse-re-max); the network sees the true Re.
+3. Training targets: the steady 256 x round(256 Ar) fields of the training draws, from one batched
+   run to --target-tol; draws that do not converge within the cap are excluded (and counted).
+4. Training: the network (lbm_net, BF16 tensor-core kernels) maps [coarse field on the fine grid,
+   Re, Ar, masks] to a correction of the fine field; Adam, mini-batches by gradient accumulation.
+5. Evaluation on the test draws, three batched runs to --tol at equal residual: from rest
+   (Sec. 2.2 i, the fallback and judge), from the interpolated coarse field, and from the network's
+   field.  Reported: steps to the tolerance per draw, their totals and ratios, and wall times.
+Prints one JSON document.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import binding as B
+from .build import build
+
+U_LID = 0.1
+NX, NXC = 256, 64
+
+
+def draws(n, seed):
+    rng = np.random.default_rng(seed)
+    return [(float(rng.uniform(100, 4000)), float(rng.uniform(0.4, 2.0))) for _ in range(n)]
+
+
+def pad16(n):
+    return (n + 15) // 16 * 16
+
+
+def batch_run(cases, dtype, tol, max_steps, init=None):
+    """cases: list of (nx, ny, Re).  init(i) -> (rho, ux, uy) device tensors or None.
+    Returns (batch handle, steps per cavity, status, wall seconds)."""
+    st = torch.cuda.current_stream()
+    b = B.lbm_batch_create([c[0] for c in cases], [c[1] for c in cases], [c[2] for c in cases],
+                           [U_LID] * len(cases), dtype)
+    B.lbm_batch_set_stream(b, st.cuda_stream)
+    if init is not None:
+        for i in range(len(cases)):
+            f = init(i)
+            if f is not None:
+                B.lbm_batch_set_moments(b, i, *f)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, done = B.lbm_batch_run_to_residual(b, len(cases), tol, max_steps)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    _, status = B.lbm_batch_residual(b, len(cases))
+    return b, done, status, wall
+
+
+def moments(b, i, nx, ny):
+    out = [torch.empty((ny, nx), dtype=torch.float64, device="cuda") for _ in range(3)]
+    B.lbm_batch_moments(b, i, *out)
+    return out
+
+
+def make_input(coarse, re, ar, ny):
+    H = pad16(ny)
+    inp = torch.empty((7, H, NX), dtype=torch.float32, device="cuda")
+    rc, ux, uy = coarse
+    B.lbm_warm_input(rc, ux, uy, NXC, rc.shape[0], re, ar, U_LID, NX, ny, H, inp,
+                     torch.cuda.current_stream().cuda_stream)
+    return inp, H
+
+
+def target_tensor(fields, ny, H):
+    rho, ux, uy = fields
+    t = torch.zeros((3, H, NX), dtype=torch.float32, device="cuda")
+    t[0, :ny] = ((rho - 1.0) * B.LBM_WARM_RHO_SCALE).float()
+    t[1, :ny] = (ux / U_LID).float()
+    t[2, :ny] = (uy / U_LID).float()
+    return t
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=400)
+    ap.add_argument("--test", type=int, default=200)
+    ap.add_argument("--width", type=int, default=20)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--dtype", default="f32s")
+    ap.add_argument("--tol", type=float, default=1e-9)
+    ap.add_argument("--target-tol", type=float, default=1e-8)
+    ap.add_argument("--max-steps", type=int, default=400_000)
+    ap.add_argument("--coarse-tol", type=float, default=1e-7)
+    ap.add_argument("--coarse-steps", type=int, default=60_000)
+    ap.add_argument("--coarse-re-max", type=float, default=1000.0)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args(argv)
+    build()
+    torch.manual_seed(0)
+    st = torch.cuda.current_stream()
+    report = {"args": vars(a)}
+    train, test = draws(a.train, 0), draws(a.test, 1)
+    allp = train + test
+
+    # 2. coarse solutions of every draw
+    cc = [(NXC, max(3, round(NXC * ar)), min(re, a.coarse_re_max)) for re, ar in allp]
+    bc, done_c, stat_c, wall_c = batch_run(cc, a.dtype, a.coarse_tol, a.coarse_steps)
+    coarse = [moments(bc, i, c[0], c[1]) for i, c in enumerate(cc)]
+    B.lbm_batch_destroy(bc)
+    for f in coarse:  # a diverged coarse run contributes nothing
+        if not all(torch.isfinite(t).all() for t in f):
+            f[0].fill_(1.0), f[1].zero_(), f[2].zero_()
+    report["coarse"] = {"wall_s": wall_c, "converged": int((stat_c == 1).sum()), "n": len(cc),
+                        "lattice_updates": int(sum(c[0] * c[1] * d for c, d in zip(cc, done_c)))}
+
+    # 3. training targets
+    tc = [(NX, round(NX * ar), re) for re, ar in train]
+    bt, done_t, stat_t, wall_t = batch_run(tc, a.dtype, a.target_tol, a.max_steps)
+    samples = []
+    for i, (re, ar) in enumerate(train):
+        if stat_t[i] != 1:
+            continue
+        ny = tc[i][1]
+        inp, H = make_input(coarse[i], re, ar, ny)
+        tgt = target_tensor(moments(bt, i, NX, ny), ny, H)
+        mask = torch.zeros((H, NX), dtype=torch.float32, device="cuda")
+        mask[:ny] = 1.0
+        samples.append((inp, inp[:3].contiguous(), tgt, mask, H))
+    B.lbm_batch_destroy(bt)
+    report["targets"] = {"wall_s": wall_t, "converged": len(samples), "excluded": a.train - len(samples),
+                         "lattice_updates": int(sum(c[0] * c[1] * d for c, d in zip(tc, done_t)))}
+
+    # 4. training
+    net = B.lbm_net_create(a.width, 0)
+    B.lbm_net_set_stream(net, st.cuda_stream)
+    rng = np.random.default_rng(2)
+    t0 = time.perf_counter()
+    history = []
+    for ep in range(a.epochs):
+        order = rng.permutation(len(samples))
+        tot = 0.0
+        lr = a.lr * 0.5 * (1 + math.cos(math.pi * ep / a.epochs))
+        for k in range(0, len(order), a.batch):
+            idx = order[k:k + a.batch]
+            B.lbm_net_zero_grads(net)
+            for j in idx:
+                inp, base, tgt, mask, H = samples[j]
+                tot += B.lbm_net_backward(net, inp, base, tgt, mask, H, NX)
+            B.lbm_net_adam_step(net, lr, grad_scale=1.0 / len(idx))
+        history.append(tot / max(1, len(samples)))
+    torch.cuda.synchronize()
+    report["training"] = {"wall_s": time.perf_counter() - t0, "params": B.lbm_net_param_count(net),
+                          "loss_first_epoch": history[0] if history else None,
+                          "loss_last_epoch": history[-1] if history else None, "history": history}
+    if a.out:
+        B.lbm_net_save(net, a.out)
+
+    # 5. evaluation: rest vs interpolated coarse vs network, all to the same tolerance
+    ec = [(NX, round(NX * ar), re) for re, ar in test]
+    off = len(train)
+    inputs = [make_input(coarse[off + i], re, ar, ec[i][1]) for i, (re, ar) in enumerate(test)]
+
+    def field_from(i, use_net):
+        nx, ny = NX, ec[i][1]
+        inp, H = inputs[i]
+        out = torch.zeros((3, H, NX), dtype=torch.float32, device="cuda")
+        if use_net:
+            B.lbm_net_forward(net, inp, H, NX, out)
+        f = [torch.empty((ny, nx), dtype=torch.float64, device="cuda") for _ in range(3)]
+        B.lbm_warm_output(inp, out, nx, ny, H, U_LID, *f, st.cuda_stream)
+        return f
+
+    arms = {}
+    for name, init in (("rest", None), ("coarse", lambda i: field_from(i, False)),
+                       ("network", lambda i: field_from(i, True))):
+        b, done, status, wall = batch_run(ec, a.dtype, a.tol, a.max_steps, init)
+        B.lbm_batch_destroy(b)
+        arms[name] = {"steps": done.tolist(), "status": status.tolist(), "wall_s": wall,
+                      "total_steps": int(done.sum()), "converged": int((status == 1).sum())}
+    both = [i for i in range(len(test)) if arms["rest"]["status"][i] == 1 and arms["network"]["status"][i] == 1]
+    ratio = [arms["network"]["steps"][i] / arms["rest"]["steps"][i] for i in both]
+    ratio_c = [arms["coarse"]["steps"][i] / arms["rest"]["steps"][i] for i in both if arms["coarse"]["status"][i] == 1]
+    report["evaluation"] = {
+        "n": len(test), "both_converged": len(both),
+        "median_steps_ratio_network_over_rest": float(np.median(ratio)) if ratio else None,
+        "mean_steps_ratio_network_over_rest": float(np.mean(ratio)) if ratio else None,
+        "median_steps_ratio_coarse_over_rest": float(np.median(ratio_c)) if ratio_c else None,
+        "fraction_network_faster": float(np.mean([r < 1 for r in ratio])) if ratio else None,
+        "total_steps": {k: v["total_steps"] for k, v in arms.items()},
+        "wall_s": {k: v["wall_s"] for k, v in arms.items()},
+        "converged": {k: v["converged"] for k, v in arms.items()},
+    }
+    report["arms"] = arms
+    report["draws_test"] = test
+    B.lbm_net_destroy(net)
+    print(json.dumps(report), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,126 @@
+"""The warm-start network's GPU kernels against the FP64 network oracle (oracle/unet.py).
+
+The oracle rounds to bfloat16 exactly the operands the GPU feeds to its tensor cores, so what
+remains is FP32 accumulation order and occasional bfloat16 rounding-boundary flips of
+intermediate activations; tolerances are stated per check.
+"""
+import numpy as np
+import pytest
+
+from oracle import unet as U
+from tests.inputs import uniform
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2211_05009_gb300 import binding as B  # noqa: E402
+
+
+@pytest.mark.parametrize("M,N,K,split", [(100, 77, 72, 1), (64, 64, 32, 1), (130, 300, 1000, 1),
+                                         (48, 200, 4096, 8), (7, 9, 8, 1)])
+def test_gemm_bf16_matches_fp64_of_bf16_inputs(M, N, K, split):
+    g = torch.Generator(device="cpu").manual_seed(M * 1000 + N)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
+    Bm = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
+    C = torch.zeros(M, N, dtype=torch.float32, device="cuda")
+    op = 2 if split > 1 else 0
+    assert B.lbm_nn_gemm_bf16(M, N, K, A, K, Bm, K, C, N, op, split) == B.LBM_OK
+    ref = A.double().cpu().numpy() @ Bm.double().cpu().numpy().T
+    err = np.abs(C.cpu().numpy() - ref).max() / np.abs(ref).max()
+    assert err < 1e-5, err
+    # accumulate adds onto C
+    assert B.lbm_nn_gemm_bf16(M, N, K, A, K, Bm, K, C, N, 1, 1) == B.LBM_OK
+    err2 = np.abs(C.cpu().numpy() - 2 * ref).max() / np.abs(ref).max()
+    assert err2 < 2e-5
+
+
+def test_gemm_rejects_unaligned_k():
+    A = torch.zeros(8, 12, dtype=torch.bfloat16, device="cuda")
+    C = torch.zeros(8, 8, dtype=torch.float32, device="cuda")
+    assert B.lbm_nn_gemm_bf16(8, 8, 12, A, 12, A, 12, C, 8, 0, 1) == B.LBM_EINVAL
+
+
+def _setup(width=4, H=64, W=64, seed=7):
+    n = B.lbm_net_create(width, 0)
+    B.lbm_net_set_stream(n, torch.cuda.current_stream().cuda_stream)
+    params = U.init_params(width, seed=seed)
+    assert B.lbm_net_param_count(n) == params.size
+    B.lbm_net_set_params(n, torch.tensor(params, dtype=torch.float32, device="cuda"))
+    x = uniform(seed, (7, H, W))
+    base = 0.3 * uniform(seed + 1, (3, H, W))
+    tgt = 0.3 * uniform(seed + 2, (3, H, W))
+    mask = (uniform(seed + 3, (H, W)) > -0.6).astype(np.float64)
+    # the oracle sees exactly the FP32 values the GPU holds
+    params32 = params.astype(np.float32).astype(np.float64)
+    arrs = [a.astype(np.float32).astype(np.float64) for a in (x, base, tgt, mask)]
+    dev = [torch.tensor(a, dtype=torch.float32, device="cuda") for a in arrs]
+    return n, params32, arrs, dev
+
+
+def test_network_forward_matches_oracle():
+    H = W = 64
+    n, p, (x, base, tgt, mask), (dx, dbase, dtgt, dmask) = _setup(H=H, W=W)
+    try:
+        out = torch.empty(3, H, W, dtype=torch.float32, device="cuda")
+        B.lbm_net_forward(n, dx, H, W, out)
+        torch.cuda.synchronize()
+        ref, _ = U.forward(p, 4, x, rnd=True)
+        got = out.double().cpu().numpy()
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        print(f"forward rel err {err:.2e}")
+        assert err < 5e-3
+    finally:
+        B.lbm_net_destroy(n)
+
+
+def test_network_loss_and_gradients_match_oracle():
+    H = W = 64
+    n, p, (x, base, tgt, mask), (dx, dbase, dtgt, dmask) = _setup(H=H, W=W)
+    try:
+        B.lbm_net_zero_grads(n)
+        loss = B.lbm_net_backward(n, dx, dbase, dtgt, dmask, H, W)
+        g = torch.empty(B.lbm_net_param_count(n), dtype=torch.float32, device="cuda")
+        B.lbm_net_get_grads(n, g)
+        g = g.double().cpu().numpy()
+        out, cache = U.forward(p, 4, x, rnd=True)
+        ref_loss, gout = U.loss_and_grad(out, base, tgt, mask)
+        ref = U.backward(p, 4, cache, gout, rnd=True)
+        assert abs(loss - ref_loss) < 1e-3 * ref_loss
+        # per convolution, weights and biases
+        off, worst = 0, 0.0
+        for ci, co in U.conv_list(4):
+            for sz in (co * ci * 9, co):
+                a, b = g[off:off + sz], ref[off:off + sz]
+                worst = max(worst, np.linalg.norm(a - b) / (np.linalg.norm(b) + 1e-30))
+                off += sz
+        print(f"loss {loss:.6e} vs {ref_loss:.6e}; worst per-tensor gradient rel err {worst:.2e}")
+        assert worst < 3e-2
+        assert np.linalg.norm(g - ref) / np.linalg.norm(ref) < 1e-2
+    finally:
+        B.lbm_net_destroy(n)
+
+
+def test_adam_training_overfits_one_sample():
+    H, W = 64, 128
+    n, p, arrs, (dx, dbase, dtgt, dmask) = _setup(H=H, W=W)
+    try:
+        losses = []
+        for it in range(60):
+            B.lbm_net_zero_grads(n)
+            losses.append(B.lbm_net_backward(n, dx, dbase, dtgt, dmask, H, W))
+            B.lbm_net_adam_step(n, 3e-3)
+        print(f"loss {losses[0]:.4e} -> {losses[-1]:.4e}")
+        assert losses[-1] < 0.1 * losses[0]
+    finally:
+        B.lbm_net_destroy(n)
+
+
+def test_network_rejects_bad_shapes():
+    n = B.lbm_net_create(4, 0)
+    try:
+        t = torch.zeros(7 * 40 * 64, dtype=torch.float32, device="cuda")
+        with pytest.raises(B.LBMError) as e:
+            B.lbm_net_forward(n, t, 40, 64, t)
+        assert e.value.code == B.LBM_EINVAL
+    finally:
+        B.lbm_net_destroy(n)
