@@ -342,6 +342,12 @@ int lbm_warm_output(const float *in, const float *out, int nx, int ny, int H, do
 int lbm_nn_gemm_bf16(int M, int N, int K, const void *A, int lda, const void *B, int ldb, float *C,
                      int ldc, int op, int split_k, void *stream);
 
+/* The same product on the 5th-generation tensor cores (tcgen05.mma with the accumulator in tensor
+ * memory, 128 x 128 tiles; no split_k).  err: DEVICE int, set to 1 if a bounded internal wait ran
+ * out (the result is then incomplete).  Asynchronous. */
+int lbm_nn_gemm_bf16_tc05(int M, int N, int K, const void *A, int lda, const void *B, int ldb,
+                          float *C, int ldc, int op, int *err, void *stream);
+
 /* ------------------------------------------------------------------ checkpoint */
 
 /* Write / read the complete state (header with nx, ny, dtype, tau, U, flags, step; the stored

@@ -104,6 +104,7 @@ _SIGS = [
     ("lbm_warm_input", _I, [_P, _P, _P, _I, _I, _D, _D, _D, _I, _I, _I, _P, _P]),
     ("lbm_warm_output", _I, [_P, _P, _I, _I, _I, _D, _P, _P, _P, _P]),
     ("lbm_nn_gemm_bf16", _I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _I, _P]),
+    ("lbm_nn_gemm_bf16_tc05", _I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _P, _P]),
     ("lbm_save", _I, [_P, ctypes.c_char_p]),
     ("lbm_load", _I, [_P, ctypes.c_char_p]),
 ]
@@ -473,3 +474,8 @@ def lbm_warm_output(inp, out, nx, ny, H, U, rho, ux, uy, stream_handle=None) -> 
 
 def lbm_nn_gemm_bf16(M, N, K, A, lda, B, ldb, C, ldc, op=0, split_k=1, stream_handle=None) -> int:
     return library().lbm_nn_gemm_bf16(M, N, K, _tptr(A), lda, _tptr(B), ldb, _tptr(C), ldc, op, split_k, stream_handle)
+
+
+def lbm_nn_gemm_bf16_tc05(M, N, K, A, lda, B, ldb, C, ldc, op, err, stream_handle=None) -> int:
+    return library().lbm_nn_gemm_bf16_tc05(M, N, K, _tptr(A), lda, _tptr(B), ldb, _tptr(C), ldc, op, _tptr(err),
+                                           stream_handle)

@@ -754,3 +754,13 @@ extern "C" int lbm_nn_gemm_bf16(int M, int N, int K, const void* A, int lda, con
     if (e == cudaErrorInvalidValue) return LBM_EINVAL;
     return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
+
+extern "C" int lbm_nn_gemm_bf16_tc05(int M, int N, int K, const void* A, int lda, const void* B, int ldb, float* C,
+                                     int ldc, int op, int* err, void* stream) {
+    if (!A || !B || !C || !err || op < 0 || op > 2) return LBM_EINVAL;
+    const cudaError_t e = gemm_bf16_nt_umma(M, N, K, static_cast<const __nv_bfloat16*>(A), lda,
+                                            static_cast<const __nv_bfloat16*>(B), ldb, C, ldc, (GemmOp)op, err,
+                                            (cudaStream_t)stream);
+    if (e == cudaErrorInvalidValue) return LBM_EINVAL;
+    return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}

@@ -34,6 +34,24 @@ def test_gemm_bf16_matches_fp64_of_bf16_inputs(M, N, K, split):
     assert err2 < 2e-5
 
 
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (200, 300, 1000), (7, 9, 8), (256, 96, 200), (130, 129, 72)])
+def test_gemm_tcgen05_matches_fp64_and_mma_sync(M, N, K):
+    g = torch.Generator(device="cpu").manual_seed(M * 7 + N * 3 + K)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
+    Bm = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
+    C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert B.lbm_nn_gemm_bf16_tc05(M, N, K, A, K, Bm, K, C, N, 0, err) == B.LBM_OK
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    ref = A.double().cpu().numpy() @ Bm.double().cpu().numpy().T
+    e = np.abs(C.cpu().numpy() - ref).max() / np.abs(ref).max()
+    assert e < 1e-5, e
+    C2 = torch.zeros(M, N, dtype=torch.float32, device="cuda")
+    assert B.lbm_nn_gemm_bf16(M, N, K, A, K, Bm, K, C2, N, 0, 1) == B.LBM_OK
+    assert torch.allclose(C, C2, rtol=1e-5, atol=1e-5 * float(np.abs(ref).max()))
+
+
 def test_gemm_rejects_unaligned_k():
     A = torch.zeros(8, 12, dtype=torch.bfloat16, device="cuda")
     C = torch.zeros(8, 8, dtype=torch.float32, device="cuda")
