@@ -1,12 +1,12 @@
 """Learned warm start for the cavity solver: data, training and evaluation.
 
-  python -m paper_2211_05009_gb300.warmstart --train 400 --test 200 --epochs 30 --out net.bin
+  python -m paper_2211_05009_gb300.warmstart --train 256 --test 64 --epochs 30 --out net.bin
 
-1. Draws (Re, Ar) with Re ~ U[100, 4000], Ar ~ U[0.4, 2.0] (training seed 0, test seed 1).
-2. Coarse solutions: every draw on 64 x round(64 Ar) nodes, run in one batch to its Eq. 6
-   tolerance or a step cap.  The coarse grid cannot resolve the highest Re (tau -> 1/2), so the
+1. Draws (Re, Ar) with Re ~ U[--re-min, --re-max], Ar ~ U[0.4, 2.0] (training seed 0, test seed 1).
+2. Coarse solutions: every draw on nxc x round(nxc Ar) nodes (nxc = nx / 4), run in one batch to
+   its Eq. 6 tolerance or a step cap.  The coarse grid cannot resolve high Re (tau -> 1/2), so the
    coarse run uses Re_c = min(Re, --coarse-re-max); the network sees the true Re.
-3. Training targets: the steady 256 x round(256 Ar) fields of the training draws, from one batched
+3. Training targets: the steady nx x round(nx Ar) fields of the training draws, from one batched
    run to --target-tol; draws that do not converge within the cap are excluded (and counted).
 4. Training: the network (lbm_net, BF16 tensor-core kernels) maps [coarse field on the fine grid,
    Re, Ar, masks] to a correction of the fine field; Adam, mini-batches by gradient accumulation.
@@ -29,12 +29,11 @@ from . import binding as B
 from .build import build
 
 U_LID = 0.1
-NX, NXC = 256, 64
 
 
-def draws(n, seed):
+def draws(n, seed, re_min, re_max):
     rng = np.random.default_rng(seed)
-    return [(float(rng.uniform(100, 4000)), float(rng.uniform(0.4, 2.0))) for _ in range(n)]
+    return [(float(rng.uniform(re_min, re_max)), float(rng.uniform(0.4, 2.0))) for _ in range(n)]
 
 
 def pad16(n):
@@ -68,18 +67,18 @@ def moments(b, i, nx, ny):
     return out
 
 
-def make_input(coarse, re, ar, ny):
+def make_input(coarse, re, ar, nx, ny):
     H = pad16(ny)
-    inp = torch.empty((7, H, NX), dtype=torch.float32, device="cuda")
+    inp = torch.empty((7, H, nx), dtype=torch.float32, device="cuda")
     rc, ux, uy = coarse
-    B.lbm_warm_input(rc, ux, uy, NXC, rc.shape[0], re, ar, U_LID, NX, ny, H, inp,
+    B.lbm_warm_input(rc, ux, uy, rc.shape[1], rc.shape[0], re, ar, U_LID, nx, ny, H, inp,
                      torch.cuda.current_stream().cuda_stream)
     return inp, H
 
 
-def target_tensor(fields, ny, H):
+def target_tensor(fields, nx, ny, H):
     rho, ux, uy = fields
-    t = torch.zeros((3, H, NX), dtype=torch.float32, device="cuda")
+    t = torch.zeros((3, H, nx), dtype=torch.float32, device="cuda")
     t[0, :ny] = ((rho - 1.0) * B.LBM_WARM_RHO_SCALE).float()
     t[1, :ny] = (ux / U_LID).float()
     t[2, :ny] = (uy / U_LID).float()
@@ -88,26 +87,30 @@ def target_tensor(fields, ny, H):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--train", type=int, default=400)
-    ap.add_argument("--test", type=int, default=200)
+    ap.add_argument("--train", type=int, default=256)
+    ap.add_argument("--test", type=int, default=64)
+    ap.add_argument("--nx", type=int, default=128, help="fine grid width (coarse: nx / 4)")
+    ap.add_argument("--re-min", type=float, default=100.0)
+    ap.add_argument("--re-max", type=float, default=1000.0)
     ap.add_argument("--width", type=int, default=20)
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=1e-3)
-    ap.add_argument("--dtype", default="f32s")
+    ap.add_argument("--dtype", default="f64", help="f64: FP32 storage stalls near 1e-6 (Eq. 6), above the tolerance")
     ap.add_argument("--tol", type=float, default=1e-9)
-    ap.add_argument("--target-tol", type=float, default=1e-8)
+    ap.add_argument("--target-tol", type=float, default=1e-9)
     ap.add_argument("--max-steps", type=int, default=400_000)
     ap.add_argument("--coarse-tol", type=float, default=1e-7)
-    ap.add_argument("--coarse-steps", type=int, default=60_000)
-    ap.add_argument("--coarse-re-max", type=float, default=1000.0)
+    ap.add_argument("--coarse-steps", type=int, default=100_000)
+    ap.add_argument("--coarse-re-max", type=float, default=400.0)
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     build()
     torch.manual_seed(0)
     st = torch.cuda.current_stream()
     report = {"args": vars(a)}
-    train, test = draws(a.train, 0), draws(a.test, 1)
+    NX, NXC = a.nx, a.nx // 4
+    train, test = draws(a.train, 0, a.re_min, a.re_max), draws(a.test, 1, a.re_min, a.re_max)
     allp = train + test
 
     # 2. coarse solutions of every draw
@@ -124,18 +127,20 @@ def main(argv=None):
     # 3. training targets
     tc = [(NX, round(NX * ar), re) for re, ar in train]
     bt, done_t, stat_t, wall_t = batch_run(tc, a.dtype, a.target_tol, a.max_steps)
+    r_t, _ = B.lbm_batch_residual(bt, len(tc))
     samples = []
     for i, (re, ar) in enumerate(train):
         if stat_t[i] != 1:
             continue
         ny = tc[i][1]
-        inp, H = make_input(coarse[i], re, ar, ny)
-        tgt = target_tensor(moments(bt, i, NX, ny), ny, H)
+        inp, H = make_input(coarse[i], re, ar, NX, ny)
+        tgt = target_tensor(moments(bt, i, NX, ny), NX, ny, H)
         mask = torch.zeros((H, NX), dtype=torch.float32, device="cuda")
         mask[:ny] = 1.0
         samples.append((inp, inp[:3].contiguous(), tgt, mask, H))
     B.lbm_batch_destroy(bt)
     report["targets"] = {"wall_s": wall_t, "converged": len(samples), "excluded": a.train - len(samples),
+                         "residual_quantiles": np.quantile(r_t, [0, 0.5, 1]).tolist(),
                          "lattice_updates": int(sum(c[0] * c[1] * d for c, d in zip(tc, done_t)))}
 
     # 4. training
@@ -166,7 +171,7 @@ def main(argv=None):
     # 5. evaluation: rest vs interpolated coarse vs network, all to the same tolerance
     ec = [(NX, round(NX * ar), re) for re, ar in test]
     off = len(train)
-    inputs = [make_input(coarse[off + i], re, ar, ec[i][1]) for i, (re, ar) in enumerate(test)]
+    inputs = [make_input(coarse[off + i], re, ar, NX, ec[i][1]) for i, (re, ar) in enumerate(test)]
 
     def field_from(i, use_net):
         nx, ny = NX, ec[i][1]
@@ -182,9 +187,11 @@ def main(argv=None):
     for name, init in (("rest", None), ("coarse", lambda i: field_from(i, False)),
                        ("network", lambda i: field_from(i, True))):
         b, done, status, wall = batch_run(ec, a.dtype, a.tol, a.max_steps, init)
+        r_end, _ = B.lbm_batch_residual(b, len(ec))
         B.lbm_batch_destroy(b)
         arms[name] = {"steps": done.tolist(), "status": status.tolist(), "wall_s": wall,
-                      "total_steps": int(done.sum()), "converged": int((status == 1).sum())}
+                      "total_steps": int(done.sum()), "converged": int((status == 1).sum()),
+                      "final_residual": r_end.tolist()}
     both = [i for i in range(len(test)) if arms["rest"]["status"][i] == 1 and arms["network"]["status"][i] == 1]
     ratio = [arms["network"]["steps"][i] / arms["rest"]["steps"][i] for i in both]
     ratio_c = [arms["coarse"]["steps"][i] / arms["rest"]["steps"][i] for i in both if arms["coarse"]["status"][i] == 1]
