@@ -173,6 +173,24 @@ def read_profile_traffic():
         return None
 
 
+def max_over_ranks(value: float, world: int) -> float:
+    """Largest value over the ranks of the default process group (the slowest rank's time);
+    works for NCCL (CUDA tensor) and gloo (CPU tensor) groups."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, seconds_max: float, world: int) -> float:
+    """Aggregate rate of `world` replicas that each processed units_per_rank in at most seconds_max."""
+    return world * units_per_rank / seconds_max
+
+
 def measured_peak():
     try:
         d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -232,12 +250,9 @@ def our_arm(args, rank, world, local_rank):
     step_kernel_s = sum(a.elapsed_time(b) for a, b in ev_chunk) / 1e3 / (CHUNK * args.steps)
     residual = B.lbm_residual(ctx)
     mass = B.lbm_mass(ctx)
-    if world > 1:
-        t = torch.tensor([elapsed], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, world)
     lu = NX * NY * CHUNK * args.steps
-    value = world * lu / elapsed / 1e9
+    value = whole_job_rate(lu, elapsed, world) / 1e9
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -264,11 +279,8 @@ def our_arm(args, rank, world, local_rank):
             e2e_step()
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([te], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": world * n * CHUNK * e2e_steps / te / 1e9, "unit": "GLUPS",
+        te = max_over_ranks(te, world)
+        e2e = {"value": whole_job_rate(n * CHUNK * e2e_steps, te, world) / 1e9, "unit": "GLUPS",
                "h2d_bytes_per_step": 3 * 8 * n, "d2h_bytes_per_step": 3 * 8 * n + 8,
                "steps": e2e_steps, "host_buffers": "pinned"}
 
