@@ -293,7 +293,7 @@ int lbm_batch_set_barrier_limit(lbm_batch *b, double seconds, int absent_block);
  * (widths w, 2w, 4w, 8w, 8w; leaky ReLU 0.1), 2x2 average pooling down, nearest x2 up with
  * skip concatenation, a 3x3 output head.  Input tensor [7][H][W] FP32 (see lbm_warm_input),
  * output [3][H][W]: corrections to input channels 0..2.  All convolutions run on BF16 tensor
- * cores with FP32 accumulation; master weights and Adam state are FP32.  H, W: multiples of 16
+ * cores (tcgen05 by default) with FP32 accumulation; master weights and Adam state are FP32.  H, W: multiples of 16
  * with (H/16)(W/16) a multiple of 8.  Tensor arguments are DEVICE pointers. */
 #define LBM_WARM_RHO_SCALE 100.0f /* channel 0 holds (rho - 1) * LBM_WARM_RHO_SCALE */
 typedef struct lbm_net lbm_net;
@@ -318,6 +318,10 @@ int lbm_net_forward(lbm_net *n, const float *in, int H, int W, float *out);
  * is 0/1; base, target [3][H][W].  *loss (host, may be NULL).  Synchronising. */
 int lbm_net_backward(lbm_net *n, const float *in, const float *base, const float *target,
                      const float *mask, int H, int W, double *loss);
+/* GEMM back end of the convolutions: 1 = tcgen05 (default; 5th-generation tensor cores, TMEM
+ * accumulator), 0 = mma.sync.  With tcgen05, lbm_net_forward synchronises, and a bounded
+ * tensor-core wait that runs out makes forward/backward return LBM_ETIMEOUT. */
+int lbm_net_set_backend(lbm_net *n, int backend);
 /* One Adam step on the accumulated gradient times grad_scale (e.g. 1/batch). */
 int lbm_net_adam_step(lbm_net *n, float lr, float beta1, float beta2, float eps, float grad_scale);
 int lbm_net_save(lbm_net *n, const char *path);
@@ -343,10 +347,11 @@ int lbm_nn_gemm_bf16(int M, int N, int K, const void *A, int lda, const void *B,
                      int ldc, int op, int split_k, void *stream);
 
 /* The same product on the 5th-generation tensor cores (tcgen05.mma with the accumulator in tensor
- * memory, 128 x 128 tiles; no split_k).  err: DEVICE int, set to 1 if a bounded internal wait ran
- * out (the result is then incomplete).  Asynchronous. */
+ * memory; 128-row tiles, N tile 32/64/128 picked from N).  trans_c != 0 stores element (m, n) at
+ * C[n*ldc + m].  split_k as above.  err: DEVICE int, set to 1 if a bounded internal wait ran out
+ * (the result is then incomplete).  Asynchronous. */
 int lbm_nn_gemm_bf16_tc05(int M, int N, int K, const void *A, int lda, const void *B, int ldb,
-                          float *C, int ldc, int op, int *err, void *stream);
+                          float *C, int ldc, int op, int trans_c, int split_k, int *err, void *stream);
 
 /* ------------------------------------------------------------------ checkpoint */
 

@@ -98,13 +98,14 @@ _SIGS = [
     ("lbm_net_zero_grads", _I, [_P]),
     ("lbm_net_forward", _I, [_P, _P, _I, _I, _P]),
     ("lbm_net_backward", _I, [_P, _P, _P, _P, _P, _I, _I, _DP]),
+    ("lbm_net_set_backend", _I, [_P, _I]),
     ("lbm_net_adam_step", _I, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
     ("lbm_net_save", _I, [_P, ctypes.c_char_p]),
     ("lbm_net_load", _I, [_P, ctypes.c_char_p]),
     ("lbm_warm_input", _I, [_P, _P, _P, _I, _I, _D, _D, _D, _I, _I, _I, _P, _P]),
     ("lbm_warm_output", _I, [_P, _P, _I, _I, _I, _D, _P, _P, _P, _P]),
     ("lbm_nn_gemm_bf16", _I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _I, _P]),
-    ("lbm_nn_gemm_bf16_tc05", _I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _P, _P]),
+    ("lbm_nn_gemm_bf16_tc05", _I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _I, _I, _P, _P]),
     ("lbm_save", _I, [_P, ctypes.c_char_p]),
     ("lbm_load", _I, [_P, ctypes.c_char_p]),
 ]
@@ -446,6 +447,10 @@ def lbm_net_backward(n, inp, base, target, mask, H: int, W: int) -> float:
     return loss.value
 
 
+def lbm_net_set_backend(n, backend: int) -> None:
+    _ncheck(n, library().lbm_net_set_backend(n, int(backend)))
+
+
 def lbm_net_adam_step(n, lr: float, beta1=0.9, beta2=0.999, eps=1e-8, grad_scale=1.0) -> None:
     _ncheck(n, library().lbm_net_adam_step(n, lr, beta1, beta2, eps, grad_scale))
 
@@ -476,6 +481,6 @@ def lbm_nn_gemm_bf16(M, N, K, A, lda, B, ldb, C, ldc, op=0, split_k=1, stream_ha
     return library().lbm_nn_gemm_bf16(M, N, K, _tptr(A), lda, _tptr(B), ldb, _tptr(C), ldc, op, split_k, stream_handle)
 
 
-def lbm_nn_gemm_bf16_tc05(M, N, K, A, lda, B, ldb, C, ldc, op, err, stream_handle=None) -> int:
-    return library().lbm_nn_gemm_bf16_tc05(M, N, K, _tptr(A), lda, _tptr(B), ldb, _tptr(C), ldc, op, _tptr(err),
-                                           stream_handle)
+def lbm_nn_gemm_bf16_tc05(M, N, K, A, lda, B, ldb, C, ldc, op, err, trans_c=0, split_k=1, stream_handle=None) -> int:
+    return library().lbm_nn_gemm_bf16_tc05(M, N, K, _tptr(A), lda, _tptr(B), ldb, _tptr(C), ldc, op, trans_c, split_k,
+                                           _tptr(err), stream_handle)

@@ -302,6 +302,8 @@ struct lbm_net {
     double* parts = nullptr;
     double* d_loss = nullptr;
     double* h_loss = nullptr;
+    int* d_err = nullptr;          // set by a tcgen05 GEMM whose bounded wait ran out
+    int backend = 1;               // 0: mma.sync GEMM, 1: tcgen05 GEMM
     cudaStream_t stream = nullptr;
     std::string err;
 
@@ -439,7 +441,14 @@ int conv_fwd(lbm_net* n, const ConvSpec& c, const float* x1, int c1, const float
     const long long P = (long long)H * W;
     k_im2col_pk<<<nblk(P * c.Kp), 256, 0, n->stream>>>(x1, c1, x2, c2, H, W, c.Kp, n->col);
     int rc = n->cuda(cudaGetLastError(), "im2col");
-    if (!rc) rc = n->cuda(gemm_bf16_nt(c.co, (int)P, c.Kp, n->wq + c.wq_off, c.Kp, n->col, c.Kp, y, (int)P, kStore, 1, n->stream), "conv gemm");
+    if (!rc) {
+        if (n->backend == 1)  // pixels on the 128-row side, channels on N, stored transposed
+            rc = n->cuda(gemm_bf16_nt_umma((int)P, c.co, c.Kp, n->col, c.Kp, n->wq + c.wq_off, c.Kp, y, (int)P, kStore, true, 1,
+                                           n->d_err, n->stream), "conv gemm (tcgen05)");
+        else
+            rc = n->cuda(gemm_bf16_nt(c.co, (int)P, c.Kp, n->wq + c.wq_off, c.Kp, n->col, c.Kp, y, (int)P, kStore, 1, n->stream),
+                         "conv gemm");
+    }
     if (!rc) {
         k_bias_act<<<nblk(c.co * P), 256, 0, n->stream>>>(y, n->params + c.boff, c.co, P, c.act);
         rc = n->cuda(cudaGetLastError(), "bias/activation");
@@ -462,18 +471,34 @@ int conv_bwd(lbm_net* n, const ConvSpec& c, const float* x1, int c1, const float
     }
     if (!rc) {
         const int split = P >= 16384 ? (int)std::min<long long>(32, P / 4096) : 1;
-        rc = n->cuda(gemm_bf16_nt(c.co, c.ci * 9, (int)P, n->dzq, (int)P, n->col, (int)P, n->grads + c.woff, c.ci * 9,
-                                  kAtomicAdd, split, n->stream), "weight-gradient gemm");
+        if (n->backend == 1)  // rows k of the k-major im2col on the 128-row side, co on N
+            rc = n->cuda(gemm_bf16_nt_umma(c.ci * 9, c.co, (int)P, n->col, (int)P, n->dzq, (int)P, n->grads + c.woff, c.ci * 9,
+                                           kAtomicAdd, true, split, n->d_err, n->stream), "weight-gradient gemm (tcgen05)");
+        else
+            rc = n->cuda(gemm_bf16_nt(c.co, c.ci * 9, (int)P, n->dzq, (int)P, n->col, (int)P, n->grads + c.woff, c.ci * 9,
+                                      kAtomicAdd, split, n->stream), "weight-gradient gemm");
     }
     // data gradient: dX[ci][p] = sum_k Wf[ci][k] dZc[p][k]
     if (!rc && (gx1 || gx2)) {
         k_im2col_pk<<<nblk(P * c.Kp2), 256, 0, n->stream>>>(n->dz, c.co, nullptr, 0, H, W, c.Kp2, n->col);
         rc = n->cuda(cudaGetLastError(), "im2col of dZ");
-        if (!rc && gx1)
-            rc = n->cuda(gemm_bf16_nt(c1, (int)P, c.Kp2, n->wf + c.wf_off, c.Kp2, n->col, c.Kp2, gx1, (int)P, kAccumulate, 1, n->stream), "data-gradient gemm");
-        if (!rc && gx2)
-            rc = n->cuda(gemm_bf16_nt(c2, (int)P, c.Kp2, n->wf + c.wf_off + (long long)c1 * c.Kp2, c.Kp2, n->col, c.Kp2, gx2, (int)P,
-                                      kAccumulate, 1, n->stream), "data-gradient gemm");
+        const __nv_bfloat16* wf1 = n->wf + c.wf_off;
+        const __nv_bfloat16* wf2 = wf1 + (long long)c1 * c.Kp2;
+        if (n->backend == 1) {
+            if (!rc && gx1)
+                rc = n->cuda(gemm_bf16_nt_umma((int)P, c1, c.Kp2, n->col, c.Kp2, wf1, c.Kp2, gx1, (int)P, kAccumulate, true, 1,
+                                               n->d_err, n->stream), "data-gradient gemm (tcgen05)");
+            if (!rc && gx2)
+                rc = n->cuda(gemm_bf16_nt_umma((int)P, c2, c.Kp2, n->col, c.Kp2, wf2, c.Kp2, gx2, (int)P, kAccumulate, true, 1,
+                                               n->d_err, n->stream), "data-gradient gemm (tcgen05)");
+        } else {
+            if (!rc && gx1)
+                rc = n->cuda(gemm_bf16_nt(c1, (int)P, c.Kp2, wf1, c.Kp2, n->col, c.Kp2, gx1, (int)P, kAccumulate, 1, n->stream),
+                             "data-gradient gemm");
+            if (!rc && gx2)
+                rc = n->cuda(gemm_bf16_nt(c2, (int)P, c.Kp2, wf2, c.Kp2, n->col, c.Kp2, gx2, (int)P, kAccumulate, 1, n->stream),
+                             "data-gradient gemm");
+        }
     }
     return rc;
 }
@@ -590,6 +615,7 @@ extern "C" int lbm_net_create(int width, unsigned long long seed, lbm_net** out)
         cudaMalloc(&n->adam_m, off * 4) != cudaSuccess || cudaMalloc(&n->adam_v, off * 4) != cudaSuccess ||
         cudaMalloc(&n->wq, q * 2) != cudaSuccess || cudaMalloc(&n->wf, f * 2) != cudaSuccess ||
         cudaMalloc(&n->parts, 1024 * sizeof(double)) != cudaSuccess || cudaMalloc(&n->d_loss, 2 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&n->d_err, sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&n->h_loss, sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         return fail("network parameter allocation");
@@ -604,7 +630,7 @@ extern "C" int lbm_net_create(int width, unsigned long long seed, lbm_net** out)
     }
     if (cudaMemcpy(n->params, h.data(), off * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(n->grads, 0, off * 4) != cudaSuccess || cudaMemset(n->adam_m, 0, off * 4) != cudaSuccess ||
-        cudaMemset(n->adam_v, 0, off * 4) != cudaSuccess) {
+        cudaMemset(n->adam_v, 0, off * 4) != cudaSuccess || cudaMemset(n->d_err, 0, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         return fail("network parameter upload");
     }
@@ -618,7 +644,7 @@ extern "C" void lbm_net_destroy(lbm_net* n) {
     for (float* p : n->act) cudaFree(p);
     for (float* p : n->gact) cudaFree(p);
     for (void* p : {(void*)n->params, (void*)n->grads, (void*)n->adam_m, (void*)n->adam_v, (void*)n->wq, (void*)n->wf,
-                    (void*)n->col, (void*)n->dz, (void*)n->dzq, (void*)n->parts, (void*)n->d_loss})
+                    (void*)n->col, (void*)n->dz, (void*)n->dzq, (void*)n->parts, (void*)n->d_loss, (void*)n->d_err})
         if (p) cudaFree(p);
     if (n->h_loss) cudaFreeHost(n->h_loss);
     delete n;
@@ -652,6 +678,23 @@ extern "C" int lbm_net_zero_grads(lbm_net* n) {
     return n->cuda(cudaMemsetAsync(n->grads, 0, n->nparams * 4, n->stream), "gradient reset");
 }
 
+// A tcgen05 GEMM that gave up waiting leaves 1 in d_err (result incomplete).
+static int check_err(lbm_net* n) {
+    int h = 0;
+    int rc = n->cuda(cudaMemcpy(&h, n->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error word copy");
+    if (!rc && h) {
+        cudaMemset(n->d_err, 0, sizeof(int));
+        return n->fail(LBM_ETIMEOUT, "a tensor-core GEMM wait ran out");
+    }
+    return rc;
+}
+
+extern "C" int lbm_net_set_backend(lbm_net* n, int backend) {
+    if (!n || backend < 0 || backend > 1) return LBM_EINVAL;
+    n->backend = backend;
+    return LBM_OK;
+}
+
 static int check_shape(lbm_net* n, int H, int W) {
     // four 2x poolings, and the pixel count of every level a multiple of 8 (GEMM rows of 16 bytes)
     if (H < 16 || W < 16 || (H & 15) || (W & 15) || ((H >> 4) * (W >> 4)) % 8)
@@ -666,6 +709,10 @@ extern "C" int lbm_net_forward(lbm_net* n, const float* in, int H, int W, float*
     if (!rc) {
         Graph g = make_graph(n->ch);
         rc = n->cuda(cudaMemcpyAsync(out, n->act[g.out], n->act_size[g.out] * 4, cudaMemcpyDeviceToDevice, n->stream), "output copy");
+    }
+    if (!rc && n->backend == 1) {
+        rc = n->cuda(cudaStreamSynchronize(n->stream), "stream synchronize");
+        if (!rc) rc = check_err(n);
     }
     return rc;
 }
@@ -687,6 +734,7 @@ extern "C" int lbm_net_backward(lbm_net* n, const float* in, const float* base, 
     if (!rc) rc = backward(n, H, W, n->dz);
     if (!rc) rc = n->cuda(cudaMemcpyAsync(n->h_loss, n->d_loss + 1, sizeof(double), cudaMemcpyDeviceToHost, n->stream), "loss copy");
     if (!rc) rc = n->cuda(cudaStreamSynchronize(n->stream), "stream synchronize");
+    if (!rc) rc = check_err(n);
     if (!rc && loss) *loss = *n->h_loss;
     return rc;
 }
@@ -756,11 +804,11 @@ extern "C" int lbm_nn_gemm_bf16(int M, int N, int K, const void* A, int lda, con
 }
 
 extern "C" int lbm_nn_gemm_bf16_tc05(int M, int N, int K, const void* A, int lda, const void* B, int ldb, float* C,
-                                     int ldc, int op, int* err, void* stream) {
+                                     int ldc, int op, int trans_c, int split_k, int* err, void* stream) {
     if (!A || !B || !C || !err || op < 0 || op > 2) return LBM_EINVAL;
     const cudaError_t e = gemm_bf16_nt_umma(M, N, K, static_cast<const __nv_bfloat16*>(A), lda,
-                                            static_cast<const __nv_bfloat16*>(B), ldb, C, ldc, (GemmOp)op, err,
-                                            (cudaStream_t)stream);
+                                            static_cast<const __nv_bfloat16*>(B), ldb, C, ldc, (GemmOp)op, trans_c != 0,
+                                            split_k, err, (cudaStream_t)stream);
     if (e == cudaErrorInvalidValue) return LBM_EINVAL;
     return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }

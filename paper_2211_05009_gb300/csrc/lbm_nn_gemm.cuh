@@ -23,11 +23,12 @@ cudaError_t gemm_bf16_nt(int M, int N, int K, const __nv_bfloat16* A, int lda,
                          const __nv_bfloat16* B, int ldb, float* C, int ldc, GemmOp op,
                          int split_k, cudaStream_t st);
 
-// The same product on the 5th-generation tensor cores (tcgen05.mma, TMEM accumulator); no split-K.
-// err: device int set to 1 if a bounded wait ran out (the result is then incomplete).
+// The same product on the 5th-generation tensor cores (tcgen05.mma, TMEM accumulator).
+// trans_c stores C[n][m] (element (m, n) at C + n*ldc + m) instead of C[m][n]; split_k > 1
+// requires kAtomicAdd.  err: device int set to 1 if a bounded wait ran out (result incomplete).
 cudaError_t gemm_bf16_nt_umma(int M, int N, int K, const __nv_bfloat16* A, int lda,
-                              const __nv_bfloat16* B, int ldb, float* C, int ldc, GemmOp op, int* err,
-                              cudaStream_t st);
+                              const __nv_bfloat16* B, int ldb, float* C, int ldc, GemmOp op, bool trans_c,
+                              int split_k, int* err, cudaStream_t st);
 
 }  // namespace nn
 }  // namespace lbm
