@@ -231,8 +231,11 @@ int lbm_stream_function_static(const double *ux, int nx, int ny, double *psi, do
  * checkpoint every active cavity gets its own Eq. 6 residual and mass; lbm_batch_run_to_residual
  * retires cavities whose residual fell below tol and compacts the work list, so converged
  * cavities cost nothing afterwards.  The launch is cooperative; every grid-barrier wait inside it
- * is bounded (default 2 s) and a wait that runs out makes the call return LBM_ETIMEOUT.
- * Device memory comes from cudaMalloc (the allocator hook applies to single cavities only). */
+ * is bounded (default 2 s) and a wait that runs out makes the call return LBM_ETIMEOUT.  A whole
+ * 100-step interval (both launches) is captured once in a CUDA graph and replayed.  Work items
+ * are (cavity, 32-lane column strip, rows per item) with a tile shape from LBM_BATCH_SHAPES
+ * (lbm_batch_autotune picks one).  Device memory comes from cudaMalloc (the allocator hook
+ * applies to single cavities only). */
 #define LBM_BATCH_MAX 512
 typedef struct lbm_batch lbm_batch;
 
@@ -277,8 +280,32 @@ int lbm_batch_set_moments(lbm_batch *b, int i, const double *rho, const double *
 int lbm_batch_probe(lbm_batch *b, const double *x, const double *y, int every, double *dev_series,
                     long cap);
 
-/* Cavity i's parameters (launch_config holds the persistent grid's block count). */
+/* Cavity i's parameters (launch_config holds the batch's tile shape). */
 int lbm_batch_info(lbm_batch *b, int i, lbm_info *info);
+
+/* Tile shapes of the batch kernel (no counterpart in the paper): rows per work item x load path x
+ * resident 128-thread blocks per SM (register budget 96 for 5, 128 for 4)
+ *   0: 2 rows, L2 loads, 5 (default)  1: 1 row, L2, 5         2: 4 rows, L2, 5
+ *   3: 2 rows, L1-cached loads, 5     4: 1 row, L1, 5         5: 4 rows, L1, 5
+ *   6: 2 rows, L1, 4                  7: 4 rows, L1, 4
+ * Every shape computes bitwise-identical populations; Eq. 6 partial sums group per item, so
+ * residuals agree to rounding.  lbm_batch_set_shape synchronises; LBM_EINVAL outside 0..7. */
+#define LBM_BATCH_SHAPES 8
+int lbm_batch_set_shape(lbm_batch *b, int shape);
+
+/* Time every tile shape for `steps` (1..10000) plain steps on the batch's current state (probes
+ * off), restore the state exactly (a temporary copy of one population pool is allocated: its
+ * size in bytes is lbm_info.device_bytes / 2 at most; LBM_ENOMEM if that fails) and keep the
+ * fastest.  chosen (host, may be NULL) receives it, ms (host [LBM_BATCH_SHAPES], may be NULL) the
+ * trial times in milliseconds.  Synchronising. */
+int lbm_batch_autotune(lbm_batch *b, int steps, int *chosen, float *ms);
+
+/* Current tile shape, its rows per item, the persistent grid's block count and the number of
+ * captured-interval replays so far (each host pointer may be NULL).  LBM_ECUDA (with the
+ * driver's message in lbm_batch_last_error) if graph capture was refused and intervals are
+ * launched directly. */
+int lbm_batch_launch_info(lbm_batch *b, int *shape, int *rows_per_item, int *blocks,
+                          long *graph_launches);
 
 /* Limit of each grid-barrier wait in seconds (default 2).  absent_block >= 0 makes that block of
  * the next launch leave before its first barrier -- a fault-injection hook for testing the

@@ -23,6 +23,7 @@ LBM_STATIC_SCRATCH_DOUBLES = 1 << 19
 DTYPES = {"f64": 0, "f32": 1, "f32s": 2, "f16s": 3, "bf16s": 4}
 LBM_FLAG_LID_CORNERS_MOVING = 1
 LBM_MAX_PROBES = 4
+LBM_BATCH_SHAPES = 8
 RESIDUAL_INTERVAL = 100
 
 
@@ -87,6 +88,9 @@ _SIGS = [
     ("lbm_batch_set_moments", _I, [_P, _I, _P, _P, _P]),
     ("lbm_batch_info", _I, [_P, _I, ctypes.POINTER(lbm_info)]),
     ("lbm_batch_set_barrier_limit", _I, [_P, _D, _I]),
+    ("lbm_batch_set_shape", _I, [_P, _I]),
+    ("lbm_batch_autotune", _I, [_P, _I, _P, _P]),
+    ("lbm_batch_launch_info", _I, [_P, _P, _P, _P, _P]),
     ("lbm_net_create", _I, [_I, ctypes.c_ulonglong, ctypes.POINTER(_P)]),
     ("lbm_net_destroy", None, [_P]),
     ("lbm_net_last_error", ctypes.c_char_p, [_P]),
@@ -382,6 +386,26 @@ def lbm_batch_info(b, i: int) -> lbm_info:
 
 def lbm_batch_set_barrier_limit(b, seconds: float, absent_block: int = -1) -> None:
     _bcheck(b, library().lbm_batch_set_barrier_limit(b, float(seconds), int(absent_block)))
+
+
+def lbm_batch_set_shape(b, shape: int) -> None:
+    _bcheck(b, library().lbm_batch_set_shape(b, int(shape)))
+
+
+def lbm_batch_autotune(b, steps: int = 50):
+    """Returns (chosen shape, trial times in ms per shape)."""
+    chosen = ctypes.c_int()
+    ms = np.zeros(LBM_BATCH_SHAPES, dtype=np.float32)
+    _bcheck(b, library().lbm_batch_autotune(b, int(steps), ctypes.byref(chosen), ms.ctypes.data))
+    return chosen.value, ms
+
+
+def lbm_batch_launch_info(b):
+    """Returns (shape, rows per item, blocks, graph replays)."""
+    sh, rows, blocks, gl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_long()
+    _bcheck(b, library().lbm_batch_launch_info(b, ctypes.byref(sh), ctypes.byref(rows), ctypes.byref(blocks),
+                                               ctypes.byref(gl)))
+    return sh.value, rows.value, blocks.value, gl.value
 
 
 # ------------------------------------------------------------------ learned warm start

@@ -13,8 +13,13 @@
 // At each checkpoint (Sec. 2.2 iii) every cavity gets its own Eq. 6 residual and mass (fixed-order
 // FP64 sums of per-item partials), cavities whose residual fell below tol -- or that reached the
 // step cap -- retire, and the active list is compacted so retired cavities cost nothing.
-// The populations of both pools are read and written within one launch, so all loads of them go
-// through L2 (ld.global.cg), never the read-only path.
+// The populations of both pools are read and written within one launch, so no load of them takes
+// the read-only path: they are either L2 loads (ld.global.cg) or weak L1-cached loads, which are
+// coherent here because every read of a pool follows the grid barrier after its last write.
+//
+// Tile shape: rows per work item (1, 2, 4) x load path (L2 / L1); lbm_batch_autotune times each
+// on the batch's own state and keeps the fastest.  Whole checkpoint intervals (the plain launch
+// and the checkpoint launch) are captured once in a CUDA graph and replayed.
 #include <cuda/atomic>
 
 #include <algorithm>
@@ -33,7 +38,14 @@ namespace lbm {
 
 constexpr int kBatchThreads = 128;
 static_assert((kBatchThreads & (kBatchThreads - 1)) == 0, "tree reductions assume a power of two");
-constexpr int kBatchR = 2;  // rows per item
+
+// Tile shapes: rows per work item x load hint (2: ld.global.cg, 3: ld.global.ca) x resident
+// blocks per SM the register budget is sized for (5: 96 registers, 4: 128).
+struct BatchShape {
+    int rows, hint, minb;
+};
+constexpr BatchShape kBatchShapes[LBM_BATCH_SHAPES] = {{2, 2, 5}, {1, 2, 5}, {4, 2, 5}, {2, 3, 5},
+                                                       {1, 3, 5}, {4, 3, 5}, {2, 3, 4}, {4, 3, 4}};
 
 struct BatchCav {
     long long off;       // population offset (storage elements) in each pool
@@ -43,7 +55,7 @@ struct BatchCav {
     double omega, U;
     float omega_f, U_f;
     int corner_moving;
-    int strips, rowgroups, items, item0;
+    int strips, items, item0;  // items = strips x ceil(ny / rows) for the current tile shape
     // one observing point per cavity (Sec. 3.3)
     int px, py, every;
     long long cap;
@@ -55,6 +67,8 @@ struct BatchState {
     int n_active;
     int err;         // 1: a barrier wait ran out
     unsigned bar_count, bar_gen;
+    double tol;          // retire when residual < tol (tol <= 0: never)
+    long long max_step;  // retire a cavity at this global step (<= 0: never)
     int active[LBM_BATCH_MAX];
     int prefix[LBM_BATCH_MAX + 1];  // exclusive prefix of item counts over the active list
     long long done_at[LBM_BATCH_MAX];  // global step of a retired cavity's state (-1: active)
@@ -70,8 +84,8 @@ struct BatchArgs {
     BatchState* st;
     double* partials;  // 3 per item, full numbering
     int nsteps;
-    double tol;           // retire when residual < tol (tol <= 0: never)
-    long long max_step;   // retire a cavity at this global step (<= 0: never)
+    int rows;             // rows per work item
+    int no_probe;         // 1: do not sample the observing points (autotuning trials)
     long long spin_limit; // barrier wait limit in clock cycles
     int absent_block;     // test hook: this block leaves at the first barrier (-1: none)
 };
@@ -113,8 +127,8 @@ __device__ __forceinline__ bool grid_barrier(BatchState* st, long long limit) {
 
 // REDUCE = false: a.nsteps plain steps (none of them a checkpoint step).  REDUCE = true: exactly
 // one step, the checkpoint step, followed by the per-cavity reduction and the compaction.
-template <typename S, bool SHIFTED, int V, bool REDUCE>
-__global__ void __launch_bounds__(kBatchThreads, 5) k_batch(const BatchArgs a) {
+template <typename S, bool SHIFTED, int V, bool REDUCE, int HINT, int MINB>
+__global__ void __launch_bounds__(kBatchThreads, MINB) k_batch(const BatchArgs a) {
     using C = typename St<S>::C;
     __shared__ int s_active[LBM_BATCH_MAX];
     __shared__ int s_prefix[LBM_BATCH_MAX + 1];
@@ -140,8 +154,11 @@ __global__ void __launch_bounds__(kBatchThreads, 5) k_batch(const BatchArgs a) {
         }
         __syncthreads();
         const int n_items = s_prefix[n];
-        const S* src_pool = static_cast<const S*>(a.pool[step & 1]);
-        S* dst_pool = static_cast<S*>(a.pool[(step + 1) & 1]);
+        // a select, not a[step & 1]: a dynamic index into the parameter array would copy the
+        // whole argument block to local memory
+        const bool odd = (step & 1) != 0;
+        const S* src_pool = static_cast<const S*>(odd ? a.pool[1] : a.pool[0]);
+        S* dst_pool = static_cast<S*>(odd ? a.pool[0] : a.pool[1]);
         for (long long item = gwarp; item < n_items; item += nwarps) {
             int lo = 0, hi = n - 1;  // largest k with prefix[k] <= item
             while (lo < hi) {
@@ -160,7 +177,7 @@ __global__ void __launch_bounds__(kBatchThreads, 5) k_batch(const BatchArgs a) {
             cv.Ulid = sizeof(C) == 4 ? C(cd.U_f) : C(cd.U);
             cv.corner_moving = cd.corner_moving;
             ProbeOne pr;
-            pr.n_ = cd.series ? 1 : 0;
+            pr.n_ = (cd.series && !a.no_probe) ? 1 : 0;
             pr.px_ = cd.px;
             pr.py_ = cd.py;
             pr.every_ = cd.every > 0 ? cd.every : 1;
@@ -173,10 +190,10 @@ __global__ void __launch_bounds__(kBatchThreads, 5) k_batch(const BatchArgs a) {
             const int x0 = (strip * 32 + lane) * V;
             C a0 = C(0), a1 = C(0), a2 = C(0);
 #pragma unroll 1
-            for (int r = 0; r < kBatchR; ++r) {
-                const int y = rg * kBatchR + r;
+            for (int r = 0; r < a.rows; ++r) {
+                const int y = rg * a.rows + r;
                 if (y >= cd.ny) break;
-                step_row<S, SHIFTED, REDUCE, V, 2>(src, dst, cv, lane, x0, y, snap, pr,
+                step_row<S, SHIFTED, REDUCE, V, HINT>(src, dst, cv, lane, x0, y, snap, pr,
                                                    [step]() { return step + 1; }, a0, a1, a2);
             }
             if constexpr (REDUCE) {
@@ -195,6 +212,8 @@ __global__ void __launch_bounds__(kBatchThreads, 5) k_batch(const BatchArgs a) {
 
         // checkpoint: per-cavity Eq. 6 and mass, in a fixed order
         __shared__ double red[3][kBatchThreads];
+        const double tol = __ldcg(&st->tol);
+        const long long max_step = __ldcg(&st->max_step);
         for (int k = blockIdx.x; k < n; k += gridDim.x) {
             const int c = s_active[k];
             const BatchCav& cd = a.cavs[c];
@@ -221,8 +240,8 @@ __global__ void __launch_bounds__(kBatchThreads, 5) k_batch(const BatchArgs a) {
                 st->mass[c] = mass;
                 int status = 0;
                 if (!isfinite(r) || !isfinite(mass)) status = 3;
-                else if (a.tol > 0.0 && r < a.tol) status = 1;
-                else if (a.max_step > 0 && step + 1 >= a.max_step) status = 2;
+                else if (tol > 0.0 && r < tol) status = 1;
+                else if (max_step > 0 && step + 1 >= max_step) status = 2;
                 st->status[c] = status;
                 if (status) st->done_at[c] = step + 1;
             }
@@ -248,8 +267,8 @@ __global__ void __launch_bounds__(kBatchThreads, 5) k_batch(const BatchArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) st->step = step0 + a.nsteps;
 }
 
-template <typename S, bool SHIFTED>
-static cudaError_t launch_batch_t(const BatchArgs& a, bool reduce, int blocks, cudaStream_t st) {
+template <typename S, bool SHIFTED, int HINT, int MINB>
+static cudaError_t launch_batch_h(const BatchArgs& a, bool reduce, int blocks, cudaStream_t st) {
     constexpr int V = sizeof(S) == 8 ? 2 : 4;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(blocks);
@@ -260,19 +279,35 @@ static cudaError_t launch_batch_t(const BatchArgs& a, bool reduce, int blocks, c
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (reduce) return cudaLaunchKernelEx(&cfg, k_batch<S, SHIFTED, V, true>, a);
-    return cudaLaunchKernelEx(&cfg, k_batch<S, SHIFTED, V, false>, a);
+    if (reduce) return cudaLaunchKernelEx(&cfg, k_batch<S, SHIFTED, V, true, HINT, MINB>, a);
+    return cudaLaunchKernelEx(&cfg, k_batch<S, SHIFTED, V, false, HINT, MINB>, a);
 }
 
 template <typename S, bool SHIFTED>
-static int batch_blocks_t() {
+static cudaError_t launch_batch_t(const BatchShape& sh, const BatchArgs& a, bool reduce, int blocks, cudaStream_t st) {
+    if (sh.hint == 2 && sh.minb == 5) return launch_batch_h<S, SHIFTED, 2, 5>(a, reduce, blocks, st);
+    if (sh.hint == 3 && sh.minb == 5) return launch_batch_h<S, SHIFTED, 3, 5>(a, reduce, blocks, st);
+    if (sh.hint == 3 && sh.minb == 4) return launch_batch_h<S, SHIFTED, 3, 4>(a, reduce, blocks, st);
+    return cudaErrorInvalidValue;
+}
+
+template <typename S, bool SHIFTED, int HINT, int MINB>
+static int batch_blocks_h() {
     constexpr int V = sizeof(S) == 8 ? 2 : 4;
     int dev = 0, sms = 0, p0 = 0, p1 = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p0, k_batch<S, SHIFTED, V, false>, kBatchThreads, 0) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, k_batch<S, SHIFTED, V, true>, kBatchThreads, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p0, k_batch<S, SHIFTED, V, false, HINT, MINB>, kBatchThreads, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, k_batch<S, SHIFTED, V, true, HINT, MINB>, kBatchThreads, 0) != cudaSuccess) return 0;
     return (p0 < p1 ? p0 : p1) * sms;  // one grid size that fits both variants
+}
+
+template <typename S, bool SHIFTED>
+static int batch_blocks_t(const BatchShape& sh) {
+    if (sh.hint == 2 && sh.minb == 5) return batch_blocks_h<S, SHIFTED, 2, 5>();
+    if (sh.hint == 3 && sh.minb == 5) return batch_blocks_h<S, SHIFTED, 3, 5>();
+    if (sh.hint == 3 && sh.minb == 4) return batch_blocks_h<S, SHIFTED, 3, 4>();
+    return 0;
 }
 
 #define LBM_BATCH_DISPATCH(dtype, CALL)                                              \
@@ -285,13 +320,13 @@ static int batch_blocks_t() {
         default: break;                                                              \
     }
 
-static cudaError_t launch_batch(int dtype, const BatchArgs& a, bool reduce, int blocks, cudaStream_t st) {
-    LBM_BATCH_DISPATCH(dtype, return (launch_batch_t<S, SH>(a, reduce, blocks, st)));
+static cudaError_t launch_batch(int dtype, const BatchShape& sh, const BatchArgs& a, bool reduce, int blocks, cudaStream_t st) {
+    LBM_BATCH_DISPATCH(dtype, return (launch_batch_t<S, SH>(sh, a, reduce, blocks, st)));
     return cudaErrorInvalidValue;
 }
 
-static int batch_blocks(int dtype) {
-    LBM_BATCH_DISPATCH(dtype, return (batch_blocks_t<S, SH>()));
+static int batch_blocks(int dtype, const BatchShape& sh) {
+    LBM_BATCH_DISPATCH(dtype, return (batch_blocks_t<S, SH>(sh)));
     return 0;
 }
 
@@ -316,20 +351,30 @@ struct lbm_batch {
     std::vector<BatchCav> cavs;
     std::vector<double> tau;
     void* pool[2] = {nullptr, nullptr};
+    size_t pool_bytes = 0;
     void* snap = nullptr;
     BatchCav* d_cavs = nullptr;
     BatchState* d_state = nullptr;
     BatchState* h_state = nullptr;  // pinned
-    double* partials = nullptr;
+    double* partials = nullptr;      // sized for one row per item (the most items)
+    int total_items = 0;             // items at one row per item
     double* psi_scratch = nullptr;
     size_t psi_doubles = 0;
     DevState* d_ext = nullptr;  // stream-function results
     DevState* h_ext = nullptr;  // pinned
-    int total_items = 0;
+    int shape = 0;              // index into kBatchShapes
     int blocks = 0;
     long long step = 0;  // host mirror of the active step
     double spin_limit_s = 2.0;
+    int absent_block = -1;
+    double dev_tol = 0.0;       // the values last written to d_state->tol / max_step
+    long long dev_max_step = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;  // private stream for graph capture
+    cudaGraphExec_t gexec = nullptr;    // one checkpoint interval
+    long long graph_key = -1;
+    long long graph_launches = 0;
+    bool graph_broken = false;
     size_t device_bytes = 0;
     std::string err;
 
@@ -370,43 +415,138 @@ struct lbm_batch {
         a.corner_moving = c.corner_moving;
         return a;
     }
+    long long spin_limit_cycles() const {
+        int dev = 0, khz = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+        return (long long)(spin_limit_s * (khz > 0 ? khz : 2000000) * 1000.0);
+    }
+    BatchArgs args(int nsteps) const {
+        BatchArgs a{};
+        a.pool[0] = pool[0];
+        a.pool[1] = pool[1];
+        a.snap = snap;
+        a.cavs = d_cavs;
+        a.st = d_state;
+        a.partials = partials;
+        a.nsteps = nsteps;
+        a.rows = kBatchShapes[shape].rows;
+        a.no_probe = 0;
+        a.spin_limit = spin_limit_cycles();
+        a.absent_block = -1;
+        return a;
+    }
+    cudaError_t launch(const BatchArgs& a, bool reduce, cudaStream_t st) const {
+        return launch_batch(dtype, kBatchShapes[shape], a, reduce, blocks, st);
+    }
+
+    // Cut every cavity into items of the shape's row count and rebuild the prefix of the active
+    // list.  Needs a current h_state (after pull_state); leaves the upload queued on the stream.
+    int relayout(int s) {
+        const int rows = kBatchShapes[s].rows;
+        const int nb = batch_blocks(dtype, kBatchShapes[s]);
+        if (nb <= 0) return fail(LBM_ECUDA, "batch kernel occupancy query failed");
+        int item0 = 0;
+        for (BatchCav& c : cavs) {
+            c.items = c.strips * ((c.ny + rows - 1) / rows);
+            c.item0 = item0;
+            item0 += c.items;
+        }
+        BatchState* h = h_state;
+        int acc = 0;
+        for (int k = 0; k < h->n_active; ++k) {
+            h->prefix[k] = acc;
+            acc += cavs[h->active[k]].items;
+        }
+        h->prefix[h->n_active] = acc;
+        int rc = cuda(cudaMemcpyAsync(d_cavs, cavs.data(), sizeof(BatchCav) * n, cudaMemcpyHostToDevice, stream), "descriptor upload");
+        if (!rc) rc = cuda(cudaMemcpyAsync(d_state->prefix, h->prefix, sizeof(int) * (h->n_active + 1), cudaMemcpyHostToDevice, stream), "prefix upload");
+        if (!rc) rc = sync();  // h_state is pinned and the source of the copy above
+        if (rc) return rc;
+        shape = s;
+        blocks = nb;
+        return LBM_OK;
+    }
+
+    // Retirement rule of the coming launches, kept in device memory so that a captured graph
+    // does not depend on it.
+    int set_retire(double tol, long long max_step) {
+        if (tol == dev_tol && max_step == dev_max_step) return LBM_OK;
+        struct { double t; long long m; } v{tol, max_step};
+        static_assert(offsetof(BatchState, max_step) == offsetof(BatchState, tol) + sizeof(double), "layout");
+        int rc = cuda(cudaMemcpyAsync(&d_state->tol, &v, sizeof v, cudaMemcpyHostToDevice, stream), "retire rule upload");
+        if (!rc) rc = sync();
+        if (rc) return rc;
+        dev_tol = tol;
+        dev_max_step = max_step;
+        return LBM_OK;
+    }
+
+    // One checkpoint interval (the plain launch of kInterval - 1 steps and the checkpoint launch),
+    // captured once per tile shape and barrier limit.  A capture the driver refuses leaves
+    // graph_broken set and the intervals are launched directly.
+    int ensure_graph() {
+        const long long key = shape * 1000003LL + (long long)(spin_limit_s * 1e6);
+        if (gexec && key == graph_key) return LBM_OK;
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        int rc = LBM_OK;
+        if (!cap_stream) rc = cuda(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking), "capture stream");
+        if (rc) return rc;
+        BatchArgs a = args(kInterval - 1);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = launch(a, false, cap_stream);
+            a.nsteps = 1;
+            if (e1 == cudaSuccess) e1 = launch(a, true, cap_stream);
+            e = cudaStreamEndCapture(cap_stream, &g);
+            if (e1 != cudaSuccess) e = e1;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            gexec = nullptr;
+            graph_broken = true;
+            err = bfmt("graph capture of the batch interval failed (%s); launching directly", cudaGetErrorString(e));
+            return LBM_OK;
+        }
+        graph_key = key;
+        return LBM_OK;
+    }
 
     // Advance every active cavity by n steps (retiring per tol / max_step at checkpoints).
     int run(long long n, double tol, long long max_step) {
-        int rc = LBM_OK;
-        long long clock_khz = 0;
-        {
-            int dev = 0, khz = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
-            clock_khz = khz > 0 ? khz : 2000000;
-        }
+        int rc = set_retire(tol, max_step);
         while (n > 0 && !rc) {
+            if (step % kInterval == 0 && n >= kInterval && absent_block < 0 && !graph_broken) {
+                rc = ensure_graph();
+                if (rc) return rc;
+                if (gexec) {
+                    rc = cuda(cudaGraphLaunch(gexec, stream), "batch graph launch");
+                    if (rc) return rc;
+                    ++graph_launches;
+                    step += kInterval;
+                    n -= kInterval;
+                    continue;
+                }
+            }
             const long long chunk = std::min<long long>(n, kInterval - step % kInterval);
-            BatchArgs a{};
-            a.pool[0] = pool[0];
-            a.pool[1] = pool[1];
-            a.snap = snap;
-            a.cavs = d_cavs;
-            a.st = d_state;
-            a.partials = partials;
-            a.nsteps = (int)chunk;
-            a.tol = tol;
-            a.max_step = max_step;
-            a.spin_limit = (long long)(spin_limit_s * clock_khz * 1000.0);
+            BatchArgs a = args((int)chunk);
             a.absent_block = absent_block;
             // plain steps first; a chunk that ends on a checkpoint ends with the REDUCE launch
             const bool ends_on_checkpoint = (step + chunk) % kInterval == 0;
             const long long plain = ends_on_checkpoint ? chunk - 1 : chunk;
             if (plain > 0) {
                 a.nsteps = (int)plain;
-                rc = cuda(launch_batch(dtype, a, false, blocks, stream), "batch kernel launch");
+                rc = cuda(launch(a, false, stream), "batch kernel launch");
                 if (rc) return rc;
                 a.absent_block = -1;
             }
             if (ends_on_checkpoint) {
                 a.nsteps = 1;
-                rc = cuda(launch_batch(dtype, a, true, blocks, stream), "batch checkpoint launch");
+                rc = cuda(launch(a, true, stream), "batch checkpoint launch");
                 if (rc) return rc;
             }
             absent_block = -1;
@@ -415,7 +555,6 @@ struct lbm_batch {
         }
         return rc;
     }
-    int absent_block = -1;
 
     int pull_state() {
         int rc = cuda(cudaMemcpyAsync(h_state, d_state, sizeof(BatchState), cudaMemcpyDeviceToHost, stream), "state copy");
@@ -433,6 +572,68 @@ struct lbm_batch {
         }
         if (!rc) step = h_state->step;
         return rc;
+    }
+
+    // Time every tile shape on the current state for `steps` plain steps (probes off), then put
+    // the state back: the current pool is saved first and restored afterwards, the other pool is
+    // rewritten by the next step anyway, retired cavities are never touched.
+    int autotune(int steps, int* chosen, float* ms_out) {
+        int rc = pull_state();
+        if (rc) return rc;
+        const int cur = shape;
+        float ms[LBM_BATCH_SHAPES];
+        for (int s = 0; s < LBM_BATCH_SHAPES; ++s) ms[s] = -1.f;
+        if (h_state->n_active == 0) {
+            if (chosen) *chosen = cur;
+            if (ms_out) std::copy(ms, ms + LBM_BATCH_SHAPES, ms_out);
+            return LBM_OK;
+        }
+        void* backup = nullptr;
+        if (cudaMalloc(&backup, pool_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LBM_ENOMEM, bfmt("autotune needs a %zu-byte copy of the populations", pool_bytes));
+        }
+        const long long step0 = step;
+        void* live = pool[step0 & 1];
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        rc = cuda(cudaMemcpyAsync(backup, live, pool_bytes, cudaMemcpyDeviceToDevice, stream), "population backup");
+        if (!rc) rc = cuda(cudaEventCreate(&e0), "event");
+        if (!rc) rc = cuda(cudaEventCreate(&e1), "event");
+        int best = -1;
+        for (int s = 0; s < LBM_BATCH_SHAPES && !rc; ++s) {
+            rc = relayout(s);
+            if (rc) break;
+            BatchArgs a = args(2);
+            a.no_probe = 1;
+            rc = cuda(launch(a, false, stream), "autotune warm-up");
+            a.nsteps = steps;
+            if (!rc) rc = cuda(cudaEventRecord(e0, stream), "event");
+            if (!rc) rc = cuda(launch(a, false, stream), "autotune trial");
+            if (!rc) rc = cuda(cudaEventRecord(e1, stream), "event");
+            if (!rc) rc = sync();
+            if (!rc) rc = cuda(cudaEventElapsedTime(&ms[s], e0, e1), "event time");
+            if (!rc) {
+                rc = pull_state();  // a barrier timeout surfaces here
+                if (!rc && (best < 0 || ms[s] < ms[best])) best = s;
+            }
+        }
+        // restore: populations, the step counter, the chosen layout
+        int rc2 = cuda(cudaMemcpyAsync(live, backup, pool_bytes, cudaMemcpyDeviceToDevice, stream), "population restore");
+        if (!rc2) {
+            h_state->step = step0;
+            rc2 = cuda(cudaMemcpyAsync(&d_state->step, &h_state->step, sizeof(long long), cudaMemcpyHostToDevice, stream), "step restore");
+        }
+        if (!rc2) rc2 = sync();
+        step = step0;
+        if (!rc2) rc2 = relayout(rc || best < 0 ? cur : best);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaFree(backup);
+        if (rc) return rc;
+        if (rc2) return rc2;
+        if (chosen) *chosen = best;
+        if (ms_out) std::copy(ms, ms + LBM_BATCH_SHAPES, ms_out);
+        return LBM_OK;
     }
 };
 
@@ -481,8 +682,7 @@ extern "C" int lbm_batch_create(int n, const int* nx, const int* ny, const doubl
         c.off = off;
         c.snap_off = soff;
         c.strips = (int)(c.pitch / (32 * V));
-        c.rowgroups = (ny[i] + kBatchR - 1) / kBatchR;
-        c.items = c.strips * c.rowgroups;
+        c.items = c.strips * ny[i];  // one row per item: the largest item count of any shape
         c.item0 = item0;
         c.series = nullptr;
         off += 9 * c.plane;
@@ -499,8 +699,9 @@ extern "C" int lbm_batch_create(int n, const int* nx, const int* ny, const doubl
         return code;
     };
     const size_t es = storage_bytes(b->dtype);
+    b->pool_bytes = (size_t)off * es;
     for (int p = 0; p < 2; ++p)
-        if (!(b->pool[p] = b->dalloc((size_t)off * es))) return fail(LBM_ENOMEM, bfmt("population pool of %zu bytes", (size_t)off * es));
+        if (!(b->pool[p] = b->dalloc(b->pool_bytes))) return fail(LBM_ENOMEM, bfmt("population pool of %zu bytes", b->pool_bytes));
     b->snap = b->dalloc((size_t)soff * arith_bytes(b->dtype));
     b->d_cavs = (BatchCav*)b->dalloc(sizeof(BatchCav) * n);
     b->d_state = (BatchState*)b->dalloc(sizeof(BatchState));
@@ -512,8 +713,6 @@ extern "C" int lbm_batch_create(int n, const int* nx, const int* ny, const doubl
     int rc = b->cuda(cudaMallocHost(&b->h_state, sizeof(BatchState)), "pinned host allocation");
     if (!rc) rc = b->cuda(cudaMallocHost(&b->h_ext, sizeof(DevState)), "pinned host allocation");
     if (rc) return fail(rc, "");
-    b->blocks = batch_blocks(b->dtype);
-    if (b->blocks <= 0) return fail(LBM_ECUDA, "batch kernel occupancy query failed");
     // initial state (Sec. 2.2 i) for every cavity, in both pools
     for (int i = 0; i < n && !rc; ++i)
         for (int p = 0; p < 2 && !rc; ++p) {
@@ -543,6 +742,7 @@ extern "C" int lbm_batch_create(int n, const int* nx, const int* ny, const doubl
     rc = b->cuda(cudaMemcpyAsync(b->d_cavs, b->cavs.data(), sizeof(BatchCav) * n, cudaMemcpyHostToDevice, b->stream), "descriptor upload");
     if (!rc) rc = b->cuda(cudaMemcpyAsync(b->d_state, h, sizeof(BatchState), cudaMemcpyHostToDevice, b->stream), "state upload");
     if (!rc) rc = b->sync();
+    if (!rc) rc = b->relayout(0);
     if (rc) return fail(rc, "");
     *out = b;
     return LBM_OK;
@@ -555,6 +755,8 @@ extern "C" void lbm_batch_destroy(lbm_batch* b) {
         if (p) cudaFree(p);
     if (b->h_state) cudaFreeHost(b->h_state);
     if (b->h_ext) cudaFreeHost(b->h_ext);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     delete b;
 }
 
@@ -715,8 +917,31 @@ extern "C" int lbm_batch_info(lbm_batch* b, int i, lbm_info* info) {
     info->flags = 0;
     info->step = (long)b->cavity_step(i);
     info->device_bytes = b->device_bytes;
-    info->launch_config = b->blocks;
+    info->launch_config = b->shape;
     return LBM_OK;
+}
+
+extern "C" int lbm_batch_set_shape(lbm_batch* b, int shape) {
+    if (!b) return LBM_EINVAL;
+    if (shape < 0 || shape >= LBM_BATCH_SHAPES) return b->fail(LBM_EINVAL, bfmt("tile shape %d: need 0..%d", shape, LBM_BATCH_SHAPES - 1));
+    int rc = b->pull_state();
+    if (!rc) rc = b->relayout(shape);
+    return rc;
+}
+
+extern "C" int lbm_batch_autotune(lbm_batch* b, int steps, int* chosen, float* ms) {
+    if (!b) return LBM_EINVAL;
+    if (steps < 1 || steps > 10000) return b->fail(LBM_EINVAL, "autotune: need 1 <= steps <= 10000");
+    return b->autotune(steps, chosen, ms);
+}
+
+extern "C" int lbm_batch_launch_info(lbm_batch* b, int* shape, int* rows_per_item, int* blocks, long* graph_launches) {
+    if (!b) return LBM_EINVAL;
+    if (shape) *shape = b->shape;
+    if (rows_per_item) *rows_per_item = kBatchShapes[b->shape].rows;
+    if (blocks) *blocks = b->blocks;
+    if (graph_launches) *graph_launches = (long)b->graph_launches;
+    return b->graph_broken ? b->fail(LBM_ECUDA, b->err) : LBM_OK;
 }
 
 extern "C" int lbm_batch_set_barrier_limit(lbm_batch* b, double seconds, int absent_block) {

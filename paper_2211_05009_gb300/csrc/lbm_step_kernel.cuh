@@ -34,13 +34,31 @@ template <> struct Raw<4> { using T = unsigned int; };
 
 // Vector load.  HINT 0: read-only path; 1: read-only with an L2 256-byte prefetch, no L1
 // allocation; 2: coherent L2 load (ld.global.cg) for kernels that also write the array they read
-// from across a grid barrier (the read-only path may serve stale lines there).
+// from across a grid barrier (the read-only path may serve stale lines there); 3: weak load cached
+// in L1 (ld.global.ca) for the same kernels -- coherent because the loads follow the barrier's
+// acquire, which discards the SM's stale L1 lines; spelled out in asm so that the compiler cannot
+// turn it into a read-only-path load.
 template <typename T, int HINT>
 __device__ __forceinline__ T ldg_vec(const T* p) {
     if constexpr (HINT == 0) {
         return __ldg(p);
     } else if constexpr (HINT == 2) {
         return __ldcg(p);
+    } else if constexpr (HINT == 3) {
+        if constexpr (sizeof(T) == 16) {
+            uint4 r;
+            asm volatile("ld.global.ca.v4.u32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+            return r;
+        } else if constexpr (sizeof(T) == 8) {
+            uint2 r;
+            asm volatile("ld.global.ca.v2.u32 {%0, %1}, [%2];" : "=r"(r.x), "=r"(r.y) : "l"(p));
+            return r;
+        } else {
+            unsigned int r;
+            asm volatile("ld.global.ca.u32 %0, [%1];" : "=r"(r) : "l"(p));
+            return r;
+        }
     } else if constexpr (sizeof(T) == 16) {
         uint4 r;
         asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0, %1, %2, %3}, [%4];"
@@ -107,10 +125,30 @@ __device__ __forceinline__ void vstore_n(S* __restrict__ p, const typename St<S>
     *reinterpret_cast<T*>(p) = b.u;
 }
 
-// Scalar load of one storage element, coherent at L2 when HINT == 2.
+// Scalar load of one storage element, coherent at L2 when HINT == 2, L1-cached weak when 3.
 template <typename S, int HINT>
 __device__ __forceinline__ typename St<S>::C lds(const S* p) {
-    if constexpr (HINT == 2) {
+    if constexpr (HINT == 3) {
+        if constexpr (sizeof(S) == 8) {
+            unsigned long long r;
+            asm volatile("ld.global.ca.u64 %0, [%1];" : "=l"(r) : "l"(p));
+            union { unsigned long long u; S s; } b;
+            b.u = r;
+            return St<S>::to(b.s);
+        } else if constexpr (sizeof(S) == 4) {
+            unsigned int r;
+            asm volatile("ld.global.ca.u32 %0, [%1];" : "=r"(r) : "l"(p));
+            union { unsigned int u; S s; } b;
+            b.u = r;
+            return St<S>::to(b.s);
+        } else {
+            unsigned short r;
+            asm volatile("ld.global.ca.u16 %0, [%1];" : "=h"(r) : "l"(p));
+            union { unsigned short u; S s; } b;
+            b.u = r;
+            return St<S>::to(b.s);
+        }
+    } else if constexpr (HINT == 2) {
         if constexpr (sizeof(S) == 8) return St<S>::to(__ldcg(reinterpret_cast<const double*>(p)));
         else if constexpr (sizeof(S) == 4) return St<S>::to(__ldcg(reinterpret_cast<const float*>(p)));
         else {

@@ -6,7 +6,8 @@ batched persistent run against one-cavity-at-a-time runs, time to steady state a
 Cavities: nx x round(nx Ar) nodes, U = 0.1 (lattice units), Re = U nx / nu.  Each runs until its
 Eq. 6 residual is below tol or max-steps steps were taken.  The batched arm steps all cavities in
 one persistent launch per 100 steps and retires converged ones; the sequential arm runs the same
-cavities one after another through the single-cavity API (lbm_run_to_residual).  Each cavity
+cavities one after another through the single-cavity API (lbm_run_to_residual).  The batched
+arm first lets lbm_batch_autotune pick its tile shape (inside its timed region).  Each cavity
 records u_x, u_y at the Sec. 3.3 observing point every `probe-every` steps, and its flow state is
 classified from that series (analysis.classify).  Prints one JSON document.
 """
@@ -35,7 +36,7 @@ def cavity_list(nx, res, ars, U):
     return cases
 
 
-def run_batched(cases, dtype, tol, max_steps, every, cap):
+def run_batched(cases, dtype, tol, max_steps, every, cap, tune_steps=50):
     st = torch.cuda.current_stream()
     b = B.lbm_batch_create([c["nx"] for c in cases], [c["ny"] for c in cases], [c["Re"] for c in cases],
                            [c["U"] for c in cases], dtype)
@@ -46,10 +47,15 @@ def run_batched(cases, dtype, tol, max_steps, every, cap):
         B.lbm_batch_probe(b, [p[0] for p in pts], [p[1] for p in pts], every, series, cap)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        tune = None
+        if tune_steps > 0:
+            chosen, ms = B.lbm_batch_autotune(b, tune_steps)
+            tune = {"chosen": chosen, "trial_ms": ms.tolist(), "steps": tune_steps}
         rc, done = B.lbm_batch_run_to_residual(b, len(cases), tol, max_steps)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         r, status = B.lbm_batch_residual(b, len(cases))
+        shape, rows, blocks, graphs = B.lbm_batch_launch_info(b)
         out = []
         ser = series.cpu().numpy()
         for i, c in enumerate(cases):
@@ -68,7 +74,9 @@ def run_batched(cases, dtype, tol, max_steps, every, cap):
                         "psi_min": psi_min, "xc": xc, "yc": yc})
         lu = sum(c["nx"] * c["ny"] * o["steps"] for c, o in zip(cases, out))
         return {"wall_s": wall, "lattice_updates": lu, "glups": lu / wall / 1e9,
-                "all_converged": rc == B.LBM_OK, "cavities": out}
+                "all_converged": rc == B.LBM_OK, "autotune": tune,
+                "launch": {"shape": shape, "rows_per_item": rows, "blocks": blocks, "graph_replays": graphs},
+                "cavities": out}
     finally:
         B.lbm_batch_destroy(b)
 
@@ -106,6 +114,7 @@ def main(argv=None):
     ap.add_argument("--max-steps", type=int, default=1_000_000)
     ap.add_argument("--probe-every", type=int, default=100)
     ap.add_argument("--sequential", action="store_true", help="also run the one-at-a-time arm")
+    ap.add_argument("--autotune-steps", type=int, default=50, help="steps per tile-shape trial (0: keep the default shape)")
     a = ap.parse_args(argv)
     build()
     res = [float(v) for v in a.re.split(",")]
@@ -114,7 +123,7 @@ def main(argv=None):
     cap = max(8, a.max_steps // a.probe_every)
     doc = {"nx": a.nx, "U": a.u, "dtype": a.dtype, "tol": a.tol, "max_steps": a.max_steps,
            "n_cavities": len(cases), "nodes": sum(c["nx"] * c["ny"] for c in cases)}
-    doc["batched"] = run_batched(cases, a.dtype, a.tol, a.max_steps, a.probe_every, cap)
+    doc["batched"] = run_batched(cases, a.dtype, a.tol, a.max_steps, a.probe_every, cap, a.autotune_steps)
     if a.sequential:
         doc["sequential"] = run_sequential(cases, a.dtype, a.tol, a.max_steps)
         doc["speedup_time_to_steady"] = doc["sequential"]["wall_s"] / doc["batched"]["wall_s"]

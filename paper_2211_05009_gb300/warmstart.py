@@ -54,6 +54,7 @@ def batch_run(cases, dtype, tol, max_steps, init=None):
                 B.lbm_batch_set_moments(b, i, *f)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    B.lbm_batch_autotune(b, 20)
     rc, done = B.lbm_batch_run_to_residual(b, len(cases), tol, max_steps)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0

@@ -64,3 +64,14 @@ def test_create_without_gpu_fails_loudly(lib):
     rc = B.library().lbm_create(16, 16, 100.0, 0.1, 2, ctypes.byref(out))
     assert rc == B.LBM_ECUDA and out.value is None
     assert "no CUDA device" in B.lbm_last_error(None)
+
+
+def test_binding_constants_match_the_header():
+    """Every integer #define of include/*.h that the binding mirrors has the header's value."""
+    seen = 0
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        for name, expr in re.findall(r"#define\s+(LBM_[A-Z0-9_]+)\s+\(?([0-9]+(?:\s*<<\s*[0-9]+)?)\)?", open(h).read()):
+            if hasattr(B, name):
+                assert getattr(B, name) == eval(expr), name
+                seen += 1
+    assert seen >= 5

@@ -138,3 +138,81 @@ def test_batch_rejects_bad_arguments():
     with pytest.raises(B.LBMError) as e:
         B.lbm_batch_create([10, 2], [10, 10], [100.0, 100.0], [0.1, 0.1], "f32s")
     assert e.value.code == B.LBM_EINVAL and "cavity 1" in str(e.value)
+
+
+def single_reference(cases, dtype, steps, probe=None):
+    """Populations, residual and (optionally) probe series of each case run alone."""
+    out = []
+    for nx, ny, re, u in cases:
+        with Cavity(nx, ny, Re=re, U=u, dtype=dtype) as cav:
+            ser = None
+            if probe:
+                q, ser = cav.probe(probe[0], probe[1], every=probe[2], cap=probe[3])
+            cav.step(steps)
+            out.append((cav.populations(host=True), cav.residual(), None if ser is None else ser.cpu().numpy()))
+    return out
+
+
+@pytest.mark.parametrize("dtype", ["f32s", "bf16s", "f64"])
+def test_every_tile_shape_matches_single_cavity(dtype):
+    """Each tile shape (rows per item, load path, blocks per SM) produces the single-cavity
+    populations and probe samples; whole checkpoint intervals run as graph replays."""
+    steps, cap, every = 250, 200, 2
+    ref = single_reference(CASES, dtype, steps, probe=(0.5, 0.3, every, cap))
+    for shape in range(B.LBM_BATCH_SHAPES):
+        b = make_batch(CASES, dtype)
+        series = torch.zeros((len(CASES), cap, 2), dtype=torch.float64, device="cuda")
+        try:
+            B.lbm_batch_set_shape(b, shape)
+            B.lbm_batch_probe(b, [0.5] * len(CASES), [0.3] * len(CASES), every, series, cap)
+            B.lbm_batch_step(b, steps)
+            sh, rows, blocks, graphs = B.lbm_batch_launch_info(b)
+            assert sh == shape and rows in (1, 2, 4) and blocks >= 152
+            assert graphs == 2, "steps 0..200 should run as two captured intervals"
+            r_b, st = B.lbm_batch_residual(b, len(CASES))
+            s_b = series.cpu().numpy()
+            for i, (nx, ny, re, u) in enumerate(CASES):
+                got = batch_pop(b, i, nx, ny)
+                pop, r_s, ser = ref[i]
+                if dtype == "f64":
+                    assert (np.abs(got - pop) / pop).max() < 1e-13, f"shape {shape} cavity {i}"
+                    assert np.allclose(s_b[i, :steps // every], ser[:steps // every], rtol=1e-12, atol=1e-16)
+                else:
+                    assert np.array_equal(got, pop), f"shape {shape} cavity {i}"
+                    assert np.array_equal(s_b[i, :steps // every], ser[:steps // every]), f"shape {shape} cavity {i}"
+                assert abs(r_b[i] - r_s) <= (1e-12 if dtype == "f64" else 1e-6) * r_s + 1e-300
+        finally:
+            B.lbm_batch_destroy(b)
+
+
+def test_autotune_leaves_the_state_unchanged():
+    """lbm_batch_autotune in the middle of an interval: the batch continues exactly as one that
+    was never tuned (populations and probe series bitwise; residual to rounding)."""
+    cases = CASES[:4]
+    cap, every = 300, 3
+    runs = []
+    for tune in (False, True):
+        b = make_batch(cases, "f32s")
+        series = torch.zeros((len(cases), cap, 2), dtype=torch.float64, device="cuda")
+        try:
+            B.lbm_batch_probe(b, [0.5] * 4, [0.4] * 4, every, series, cap)
+            B.lbm_batch_step(b, 150)
+            chosen = None
+            if tune:
+                chosen, ms = B.lbm_batch_autotune(b, 20)
+                assert 0 <= chosen < B.LBM_BATCH_SHAPES and (ms > 0).all()
+                assert ms[chosen] == ms.min()
+                assert B.lbm_batch_launch_info(b)[0] == chosen
+            B.lbm_batch_step(b, 250)
+            r, _ = B.lbm_batch_residual(b, len(cases))
+            pops = [batch_pop(b, i, c[0], c[1]) for i, c in enumerate(cases)]
+            steps = B.lbm_batch_cavity_steps(b, len(cases))
+            runs.append((pops, series.cpu().numpy(), r, steps))
+        finally:
+            B.lbm_batch_destroy(b)
+    (p0, s0, r0, t0), (p1, s1, r1, t1) = runs
+    assert (t0 == 400).all() and (t1 == 400).all()
+    for a, c in zip(p0, p1):
+        assert np.array_equal(a, c)
+    assert np.array_equal(s0, s1)
+    assert np.allclose(r0, r1, rtol=1e-6, atol=0)
