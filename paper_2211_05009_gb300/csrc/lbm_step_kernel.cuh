@@ -20,6 +20,8 @@
 // padding nodes (x >= nx) store the rest state.
 #pragma once
 
+#include <type_traits>
+
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 
@@ -210,7 +212,15 @@ __device__ __forceinline__ void geq9(C drho, C rho, C ux, C uy, C (&e)[9]) {
 
 template <typename C>
 __device__ __forceinline__ C rcp(C v);
-template <> __device__ __forceinline__ float rcp<float>(float v) { return __frcp_rn(v); }
+// FP32: hardware reciprocal estimate refined by one Newton-Raphson step r + r(1 - v r) (error
+// below one ulp for the densities rho ~ 1 met here; no subnormals).  The IEEE-rounded reciprocal
+// costs several times the instructions in a kernel that is partly issue-bound.
+template <> __device__ __forceinline__ float rcp<float>(float v) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    const float e = fmaf(-v, r, 1.0f);
+    return fmaf(r, e, r);
+}
 template <> __device__ __forceinline__ double rcp<double>(double v) { return __drcp_rn(v); }
 
 // Streamed populations of one row segment (V nodes) of row y, walls folded in: wall rows gather
@@ -315,8 +325,12 @@ __device__ __forceinline__ void step_row(const S* __restrict__ src, S* __restric
     unsigned pmask = 0;
     for (int q = 0; q < probes.n(); ++q)
         if (probes.py(q) == y && probes.px(q) >= x0 && probes.px(q) < x0 + V) pmask |= 1u << q;
-#pragma unroll
-    for (int i = 0; i < V; ++i) {
+    // Per node.  EDGE = false: the whole segment is interior (no wall, lid or padding node), the
+    // case of all but the first and last lanes of a row, so the wall tests compile away; the
+    // arithmetic is the same either way.  Only 4- and 8-byte storage takes the split: for 16-bit
+    // storage the kernel is issue-bound and the second copy of the node code measured slower.
+    auto node = [&](auto edge_c, int i) {
+        constexpr bool EDGE = decltype(edge_c)::value;
         const int x = x0 + i;
         C g[9];
 #pragma unroll
@@ -329,7 +343,7 @@ __device__ __forceinline__ void step_row(const S* __restrict__ src, S* __restric
         const C ux = jx * inv, uy = jy * inv;
         C e[9];
         geq9<C>(drho, rho, ux, uy, e);
-        const bool wall = (y == 0) | (y == ny - 1) | (x == 0) | (x >= nx - 1);
+        const bool wall = EDGE && ((y == 0) | (y == ny - 1) | (x == 0) | (x >= nx - 1));
         C uox = ux, uoy = uy;
         if (wall) {
             const bool lid = (y == ny - 1) && (cv.corner_moving || (x > 0 && x < nx - 1));
@@ -358,19 +372,19 @@ __device__ __forceinline__ void step_row(const S* __restrict__ src, S* __restric
 #pragma unroll
             for (int j = 0; j < 9; ++j) f[j][i] = g[j] + d[j];
         }
-        if (x >= nx) {
+        if (EDGE && x >= nx) {
 #pragma unroll
             for (int j = 0; j < 9; ++j) f[j][i] = C(0.0);
         }
         if constexpr (REDUCE) {
-            if (x < nx) {
+            if (!EDGE || x < nx) {
                 const C dx = uox - sx[i], dy = uoy - sy[i];  // exact when close (Sterbenz)
                 acc_drho += drho;
                 acc_num += dx * dx + dy * dy;
                 acc_den += sx[i] * sx[i] + sy[i] * sy[i];
             }
-            sx[i] = x < nx ? uox : C(0);
-            sy[i] = x < nx ? uoy : C(0);
+            sx[i] = (!EDGE || x < nx) ? uox : C(0);
+            sy[i] = (!EDGE || x < nx) ? uoy : C(0);
         }
         if (pmask) {
             for (int q = 0; q < probes.n(); ++q) {
@@ -388,6 +402,13 @@ __device__ __forceinline__ void step_row(const S* __restrict__ src, S* __restric
                 }
             }
         }
+    };
+    if (sizeof(S) < 4 || (y == 0) | (y == ny - 1) | (x0 == 0) | (x0 + V >= nx)) {
+#pragma unroll
+        for (int i = 0; i < V; ++i) node(std::true_type{}, i);
+    } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i) node(std::false_type{}, i);
     }
 
     S* pd = dst + (long long)y * pitch + x0;
