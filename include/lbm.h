@@ -156,6 +156,16 @@ int lbm_moments(lbm_ctx *ctx, double *rho, double *ux, double *uy);
  * e.g. a warm start).  Inputs [ny][nx] FP64; resets the step count and the Eq. 6 snapshot. */
 int lbm_set_moments(lbm_ctx *ctx, const double *rho, const double *ux, const double *uy);
 
+/* lbm_set_moments with options.  LBM_INIT_NEQ (no counterpart in the paper; a consistent warm
+ * start after the first-order Chapman-Enskog expansion of BGK): the post-collision state becomes
+ *   f*_j = f^eq_j(rho, u) + (1 - 1/tau) f^neq_j,
+ *   f^neq_j = -tau w_j rho / c_s^2 (c_ja c_jb - c_s^2 delta_ab) d_a u_b,   c_s^2 = 1/3,
+ * with d_a u_b from central differences inside and three-point one-sided differences on the ring
+ * (both exact for quadratic fields), so the start already carries the stress of its velocity field.
+ * The moments are still (rho, u).  flags = 0 is lbm_set_moments.  LBM_EINVAL for unknown flags. */
+#define LBM_INIT_NEQ 1
+int lbm_set_moments_ex(lbm_ctx *ctx, const double *rho, const double *ux, const double *uy, int flags);
+
 /* Current post-collision populations as FP64 f_j (not deviations), [9][ny][nx]. */
 int lbm_get_populations(lbm_ctx *ctx, double *f);
 
@@ -273,6 +283,9 @@ int lbm_batch_stream_function(lbm_batch *b, int i, double *psi, double *psi_min,
  * start); its Eq. 6 snapshot becomes u.  Only for an active cavity while the batch sits on a
  * checkpoint boundary (step multiple of 100, e.g. right after lbm_batch_create).  Synchronising. */
 int lbm_batch_set_moments(lbm_batch *b, int i, const double *rho, const double *ux, const double *uy);
+/* The same with the flags of lbm_set_moments_ex (LBM_INIT_NEQ uses cavity i's tau). */
+int lbm_batch_set_moments_ex(lbm_batch *b, int i, const double *rho, const double *ux, const double *uy,
+                             int flags);
 
 /* One observing point per cavity at (x[i], y[i]) (width units, as lbm_probe); after every step
  * t with t % every == 0 cavity i writes (u_x, u_y) to dev_series[2 (i cap + k)], k = sample

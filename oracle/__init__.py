@@ -71,6 +71,7 @@ def _L():
         lib.orc_step_node.argtypes = [pp, dp, ctypes.c_int, ctypes.c_int, dp]
         lib.orc_init.argtypes = [pp, dp]
         lib.orc_init_moments.argtypes = [pp, dp, dp, dp, dp]
+        lib.orc_init_moments_neq.argtypes = [pp, dp, dp, dp, dp]
         lib.orc_moments.argtypes = [pp, dp, dp, dp, dp]
         lib.orc_residual.argtypes = [ctypes.c_size_t, dp, dp, dp, dp]
         lib.orc_residual.restype = ctypes.c_double
@@ -129,6 +130,15 @@ def init_moments(p: Params, rho, ux, uy) -> np.ndarray:
     rho, ux, uy = (np.ascontiguousarray(a, dtype=np.float64) for a in (rho, ux, uy))
     f = np.zeros((p.ny, p.nx, 9))
     _L().orc_init_moments(ctypes.byref(p.c()), _dp(rho), _dp(ux), _dp(uy), _dp(f))
+    return f
+
+
+def init_moments_neq(p: Params, rho, ux, uy) -> np.ndarray:
+    """f^eq(rho, u) plus (1 - 1/tau) times the first-order Chapman-Enskog non-equilibrium part
+    built from the velocity gradients (not in the paper; a consistent warm start)."""
+    rho, ux, uy = (np.ascontiguousarray(a, dtype=np.float64) for a in (rho, ux, uy))
+    f = np.zeros((p.ny, p.nx, 9))
+    _L().orc_init_moments_neq(ctypes.byref(p.c()), _dp(rho), _dp(ux), _dp(uy), _dp(f))
     return f
 
 

@@ -226,6 +226,50 @@ void orc_init_moments(const orc_params *p, const double *rho, const double *ux, 
     for (size_t k = 0; k < n; ++k) orc_feq(rho[k], ux[k], uy[k], &f[k * 9]);
 }
 
+/* Derivative along one grid line of a node field (grid spacing 1): central difference
+ * (a[i+1] - a[i-1]) / 2 inside, the three-point one-sided formula (-3 a0 + 4 a1 - a2) / 2 (and
+ * its mirror) at the two end nodes; both exact for quadratics.  line[k * stride] is node k. */
+static double d_line(const double *line, size_t stride, int i, int n)
+{
+    if (i == 0) return (-3.0 * line[0] + 4.0 * line[stride] - line[2 * stride]) / 2.0;
+    if (i == n - 1)
+        return (3.0 * line[(size_t)(n - 1) * stride] - 4.0 * line[(size_t)(n - 2) * stride] +
+                line[(size_t)(n - 3) * stride]) / 2.0;
+    return (line[(size_t)(i + 1) * stride] - line[(size_t)(i - 1) * stride]) / 2.0;
+}
+
+/* Not part of the paper: a post-collision state consistent with given macroscopic fields to
+ * first order in the Chapman-Enskog expansion of BGK (a warm start that does not begin with a
+ * stress-free field).  Pre-collision f = f^eq + f^neq with
+ *     f^neq_j = -tau w_j rho / c_s^2 (c_ja c_jb - c_s^2 delta_ab) d_a u_b,   c_s^2 = 1/3,
+ * and one BGK collision keeps (1 - 1/tau) of it:  f*_j = f^eq_j(rho, u) + (1 - 1/tau) f^neq_j.
+ * f^neq carries no mass or momentum, so the moments of f* are (rho, u).  Derivatives by d_line;
+ * needs nx, ny >= 3. */
+void orc_init_moments_neq(const orc_params *p, const double *rho, const double *ux, const double *uy,
+                          double *f)
+{
+    const double cs2 = 1.0 / 3.0;
+    const double keep = 1.0 - 1.0 / p->tau;
+    for (int y = 0; y < p->ny; ++y)
+        for (int x = 0; x < p->nx; ++x) {
+            const size_t k = node(p, x, y);
+            const double *rx = ux + (size_t)y * (size_t)p->nx, *ry = uy + (size_t)y * (size_t)p->nx;
+            const double dxux = d_line(rx, 1, x, p->nx), dxuy = d_line(ry, 1, x, p->nx);
+            const double dyux = d_line(ux + x, (size_t)p->nx, y, p->ny);
+            const double dyuy = d_line(uy + x, (size_t)p->nx, y, p->ny);
+            double *fk = &f[k * 9];
+            orc_feq(rho[k], ux[k], uy[k], fk);
+            for (int j = 0; j < 9; ++j) {
+                const double qxx = CX[j] * CX[j] - cs2, qyy = CY[j] * CY[j] - cs2;
+                const double qxy = (double)(CX[j] * CY[j]);
+                /* Q:grad u = Q_ab d_a u_b, Q symmetric */
+                const double qdu = qxx * dxux + qxy * (dxuy + dyux) + qyy * dyuy;
+                const double fneq = -p->tau * W[j] * rho[k] / cs2 * qdu;
+                fk[j] += keep * fneq;
+            }
+        }
+}
+
 /* Eq. 3 at every node of a post-collision field.  Wall nodes report (rho_f, u_w), the
  * moments their post-collision populations carry. */
 void orc_moments(const orc_params *p, const double *f, double *rho, double *ux, double *uy)

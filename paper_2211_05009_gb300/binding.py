@@ -24,6 +24,7 @@ DTYPES = {"f64": 0, "f32": 1, "f32s": 2, "f16s": 3, "bf16s": 4}
 LBM_FLAG_LID_CORNERS_MOVING = 1
 LBM_MAX_PROBES = 4
 LBM_BATCH_SHAPES = 8
+LBM_INIT_NEQ = 1
 RESIDUAL_INTERVAL = 100
 
 
@@ -62,6 +63,7 @@ _SIGS = [
     ("lbm_run_to_residual", _I, [_P, _D, _L, ctypes.POINTER(_L)]),
     ("lbm_moments", _I, [_P, _P, _P, _P]),
     ("lbm_set_moments", _I, [_P, _P, _P, _P]),
+    ("lbm_set_moments_ex", _I, [_P, _P, _P, _P, _I]),
     ("lbm_get_populations", _I, [_P, _P]),
     ("lbm_set_populations", _I, [_P, _P]),
     ("lbm_residual", _I, [_P, _DP]),
@@ -86,6 +88,7 @@ _SIGS = [
     ("lbm_batch_stream_function", _I, [_P, _I, _P, _DP, _DP, _DP]),
     ("lbm_batch_probe", _I, [_P, _P, _P, _I, _P, _L]),
     ("lbm_batch_set_moments", _I, [_P, _I, _P, _P, _P]),
+    ("lbm_batch_set_moments_ex", _I, [_P, _I, _P, _P, _P, _I]),
     ("lbm_batch_info", _I, [_P, _I, ctypes.POINTER(lbm_info)]),
     ("lbm_batch_set_barrier_limit", _I, [_P, _D, _I]),
     ("lbm_batch_set_shape", _I, [_P, _I]),
@@ -226,8 +229,8 @@ def lbm_moments(ctx, rho=None, ux=None, uy=None) -> None:
     _check(ctx, library().lbm_moments(ctx, _ptr(rho), _ptr(ux), _ptr(uy)))
 
 
-def lbm_set_moments(ctx, rho, ux, uy) -> None:
-    _check(ctx, library().lbm_set_moments(ctx, _ptr(rho), _ptr(ux), _ptr(uy)))
+def lbm_set_moments(ctx, rho, ux, uy, flags: int = 0) -> None:
+    _check(ctx, library().lbm_set_moments_ex(ctx, _ptr(rho), _ptr(ux), _ptr(uy), int(flags)))
 
 
 def lbm_get_populations(ctx, f) -> None:
@@ -368,8 +371,8 @@ def lbm_batch_stream_function(b, i: int, psi=None):
     return vmin.value, xc.value, yc.value
 
 
-def lbm_batch_set_moments(b, i: int, rho, ux, uy) -> None:
-    _bcheck(b, library().lbm_batch_set_moments(b, i, _ptr(rho), _ptr(ux), _ptr(uy)))
+def lbm_batch_set_moments(b, i: int, rho, ux, uy, flags: int = 0) -> None:
+    _bcheck(b, library().lbm_batch_set_moments_ex(b, i, _ptr(rho), _ptr(ux), _ptr(uy), int(flags)))
 
 
 def lbm_batch_probe(b, x, y, every: int, dev_series, cap: int) -> None:

@@ -93,8 +93,8 @@ class Cavity:
     def set_populations(self, f):
         B.lbm_set_populations(self.ctx, f)
 
-    def set_moments(self, rho, ux, uy):
-        B.lbm_set_moments(self.ctx, rho, ux, uy)
+    def set_moments(self, rho, ux, uy, neq: bool = False):
+        B.lbm_set_moments(self.ctx, rho, ux, uy, B.LBM_INIT_NEQ if neq else 0)
 
     def residual(self) -> float:
         return B.lbm_residual(self.ctx)

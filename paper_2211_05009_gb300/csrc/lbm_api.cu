@@ -553,7 +553,12 @@ extern "C" int lbm_moments(lbm_ctx* c, double* rho, double* ux, double* uy) {
 }
 
 extern "C" int lbm_set_moments(lbm_ctx* c, const double* rho, const double* ux, const double* uy) {
+    return lbm_set_moments_ex(c, rho, ux, uy, 0);
+}
+
+extern "C" int lbm_set_moments_ex(lbm_ctx* c, const double* rho, const double* ux, const double* uy, int flags) {
     if (!c || !rho || !ux || !uy) return c ? c->fail(LBM_EINVAL, "NULL field") : LBM_EINVAL;
+    if (flags & ~LBM_INIT_NEQ) return c->fail(LBM_EINVAL, "unknown lbm_set_moments_ex flag");
     const size_t bytes = (size_t)c->nx * c->ny * sizeof(double);
     int rc = c->ensure_stage(3 * bytes);
     if (rc) return rc;
@@ -572,7 +577,8 @@ extern "C" int lbm_set_moments(lbm_ctx* c, const double* rho, const double* ux, 
     c->step = 0;
     for (int q = 0; q < c->probes.n; ++q) c->probes.start[q] = 0;
     c->invalidate_graphs();
-    rc = c->cuda(launch_set_moments(c->dtype, c->cur(), dv[0], dv[1], dv[2], c->snap, c->stream), "set_moments launch");
+    rc = c->cuda(launch_set_moments(c->dtype, c->cur(), dv[0], dv[1], dv[2], c->snap,
+                                    (flags & LBM_INIT_NEQ) ? c->tau : 0.0, c->stream), "set_moments launch");
     if (!rc) rc = c->cuda(cudaMemsetAsync(c->d_state, 0, sizeof(DevState), c->stream), "state reset");
     if (!rc && off) rc = c->sync();  // the staged host input may be reused after return
     return rc;

@@ -53,9 +53,21 @@ __device__ __forceinline__ void node_moments(const S* f, long long plane, long l
 }
 
 // ------------------------------------------------------------------ init / set_moments
+// d/dk of a node field along one grid line (spacing 1): central inside, three-point one-sided
+// at the two ends (both exact for quadratics).  line[k * stride] is node k; n >= 3.
+__device__ __forceinline__ double d_line(const double* line, long long stride, int i, int n) {
+    if (i == 0) return (-3.0 * line[0] + 4.0 * line[stride] - line[2 * stride]) * 0.5;
+    if (i == n - 1)
+        return (3.0 * line[(n - 1) * stride] - 4.0 * line[(n - 2) * stride] + line[(n - 3) * stride]) * 0.5;
+    return (line[(i + 1) * stride] - line[(i - 1) * stride]) * 0.5;
+}
+
+// neq_tau > 0 (only with given fields): add (1 - 1/tau) f^neq_j, the first-order Chapman-Enskog
+// non-equilibrium part f^neq_j = -tau w_j rho / c_s^2 (c_ja c_jb - c_s^2 delta_ab) d_a u_b of BGK,
+// so that the start carries the stress of its velocity field (no counterpart in the paper).
 template <typename S, bool SHIFTED>
 __global__ void k_init(FieldArgs a, void* snap_v, const double* rho_in, const double* ux_in,
-                       const double* uy_in) {
+                       const double* uy_in, double neq_tau) {
     using C = typename St<S>::C;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
@@ -63,19 +75,35 @@ __global__ void k_init(FieldArgs a, void* snap_v, const double* rho_in, const do
     S* f = static_cast<S*>(a.f);
     const long long k = (long long)y * a.pitch + x;
     C drho = C(0), ux = C(0), uy = C(0);
+    C dxux = C(0), dyux = C(0), dxuy = C(0), dyuy = C(0);
+    const bool neq = neq_tau > 0.0 && rho_in && x < a.nx;
     if (x < a.nx) {
         if (rho_in) {
             const long long d = (long long)y * a.nx + x;
             drho = C(rho_in[d] - 1.0);
             ux = C(ux_in[d]);
             uy = C(uy_in[d]);
+            if (neq) {
+                const long long row = (long long)y * a.nx;
+                dxux = C(d_line(ux_in + row, 1, x, a.nx));
+                dxuy = C(d_line(uy_in + row, 1, x, a.nx));
+                dyux = C(d_line(ux_in + x, a.nx, y, a.ny));
+                dyuy = C(d_line(uy_in + x, a.nx, y, a.ny));
+            }
         } else if (y == a.ny - 1 && (a.corner_moving || (x > 0 && x < a.nx - 1))) {
             ux = C(a.U);  // Sec. 2.2 (i): only the lid moves at t = 0
         }
     }
+    const C tau = C(neq_tau), keep = neq ? C(1.0) - C(1.0) / tau : C(0);
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
-        const C g = geq_c<C>(j, drho, ux, uy);
+        C g = geq_c<C>(j, drho, ux, uy);
+        if (neq) {
+            const C third = C(1.0 / 3.0);
+            const C qxx = C(cx(j) * cx(j)) - third, qyy = C(cy(j) * cy(j)) - third, qxy = C(cx(j) * cy(j));
+            const C qdu = qxx * dxux + qxy * (dxuy + dyux) + qyy * dyuy;
+            g += keep * (-C(3.0) * tau * C(wd(j)) * (C(1.0) + drho) * qdu);
+        }
         f[j * a.plane + k] = St<S>::from(SHIFTED ? g : g + C(wd(j)));
     }
     if (snap_v) {
@@ -288,14 +316,14 @@ size_t psi_scratch_doubles(int nx, int ny) {
 
 cudaError_t launch_init(int dtype, const FieldArgs& a, void* snap, cudaStream_t st) {
     dim3 grid((unsigned)((a.pitch + 127) / 128), a.ny);
-    LBM_DISPATCH(dtype, (k_init<S, SH><<<grid, 128, 0, st>>>(a, snap, nullptr, nullptr, nullptr)));
+    LBM_DISPATCH(dtype, (k_init<S, SH><<<grid, 128, 0, st>>>(a, snap, nullptr, nullptr, nullptr, 0.0)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_set_moments(int dtype, const FieldArgs& a, const double* rho, const double* ux,
-                               const double* uy, void* snap, cudaStream_t st) {
+                               const double* uy, void* snap, double neq_tau, cudaStream_t st) {
     dim3 grid((unsigned)((a.pitch + 127) / 128), a.ny);
-    LBM_DISPATCH(dtype, (k_init<S, SH><<<grid, 128, 0, st>>>(a, snap, rho, ux, uy)));
+    LBM_DISPATCH(dtype, (k_init<S, SH><<<grid, 128, 0, st>>>(a, snap, rho, ux, uy, neq_tau)));
     return cudaGetLastError();
 }
 

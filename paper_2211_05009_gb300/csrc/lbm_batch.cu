@@ -952,7 +952,13 @@ extern "C" int lbm_batch_set_barrier_limit(lbm_batch* b, double seconds, int abs
 }
 
 extern "C" int lbm_batch_set_moments(lbm_batch* b, int i, const double* rho, const double* ux, const double* uy) {
+    return lbm_batch_set_moments_ex(b, i, rho, ux, uy, 0);
+}
+
+extern "C" int lbm_batch_set_moments_ex(lbm_batch* b, int i, const double* rho, const double* ux, const double* uy,
+                                        int flags) {
     if (!b || i < 0 || i >= b->n || !rho || !ux || !uy) return b ? b->fail(LBM_EINVAL, "bad arguments") : LBM_EINVAL;
+    if (flags & ~LBM_INIT_NEQ) return b->fail(LBM_EINVAL, "unknown lbm_batch_set_moments_ex flag");
     int rc = b->pull_state();
     if (rc) return rc;
     for (const double* p : {rho, ux, uy}) {
@@ -966,7 +972,8 @@ extern "C" int lbm_batch_set_moments(lbm_batch* b, int i, const double* rho, con
         return b->fail(LBM_EINVAL, "cavity retired, or the batch is not at a checkpoint boundary");
     const BatchCav& c = b->cavs[i];
     void* sp = (char*)b->snap + c.snap_off * arith_bytes(b->dtype);
-    rc = b->cuda(launch_set_moments(b->dtype, b->field(i), rho, ux, uy, sp, b->stream), "set_moments launch");
+    rc = b->cuda(launch_set_moments(b->dtype, b->field(i), rho, ux, uy, sp, (flags & LBM_INIT_NEQ) ? b->tau[i] : 0.0,
+                                    b->stream), "set_moments launch");
     if (!rc) rc = b->sync();
     return rc;
 }

@@ -45,9 +45,10 @@ struct FieldArgs {
 
 // f = f^eq(1, u0) with the Sec. 2.2 (i) initial velocity; snapshot = u0.
 cudaError_t launch_init(int dtype, const FieldArgs& a, void* snap, cudaStream_t st);
-// f = f^eq(rho, u) from dense [ny][nx] FP64 fields; snapshot = u.
+// f = f^eq(rho, u) from dense [ny][nx] FP64 fields; snapshot = u.  neq_tau > 0 adds
+// (1 - 1/tau) times the first-order Chapman-Enskog non-equilibrium part (tau = neq_tau).
 cudaError_t launch_set_moments(int dtype, const FieldArgs& a, const double* rho, const double* ux,
-                               const double* uy, void* snap, cudaStream_t st);
+                               const double* uy, void* snap, double neq_tau, cudaStream_t st);
 // Dense [ny][nx] FP64 moments (any output may be null).
 cudaError_t launch_moments(int dtype, const FieldArgs& a, double* rho, double* ux, double* uy,
                            cudaStream_t st);

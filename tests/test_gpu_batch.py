@@ -216,3 +216,26 @@ def test_autotune_leaves_the_state_unchanged():
         assert np.array_equal(a, c)
     assert np.array_equal(s0, s1)
     assert np.allclose(r0, r1, rtol=1e-6, atol=0)
+
+
+def test_batch_set_moments_neq_matches_single_cavity():
+    """lbm_batch_set_moments_ex(LBM_INIT_NEQ) gives cavity i the single-cavity warm start, and
+    both continue identically."""
+    from tests.inputs import uniform
+    cases = CASES[:3]
+    b = make_batch(cases, "f32s")
+    fields = []
+    try:
+        for i, (nx, ny, re, u) in enumerate(cases):
+            r = uniform(10 + i, (3, ny, nx))
+            fl = [torch.from_numpy(a).cuda() for a in (1 + 0.01 * r[0], 0.03 * r[1], 0.03 * r[2])]
+            fields.append(fl)
+            B.lbm_batch_set_moments(b, i, *fl, flags=B.LBM_INIT_NEQ)
+        B.lbm_batch_step(b, 130)
+        for i, (nx, ny, re, u) in enumerate(cases):
+            with Cavity(nx, ny, Re=re, U=u, dtype="f32s") as cav:
+                cav.set_moments(*fields[i], neq=True)
+                cav.step(130)
+                assert np.array_equal(batch_pop(b, i, nx, ny), cav.populations(host=True)), f"cavity {i}"
+    finally:
+        B.lbm_batch_destroy(b)

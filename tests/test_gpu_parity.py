@@ -152,6 +152,25 @@ def test_set_moments_gives_equilibrium():
     assert np.abs(f - ref).max() < 1e-16 * 8
 
 
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-13), ("f32s", 3e-7), ("f32", 3e-7), ("f16s", 2e-3)])
+def test_set_moments_neq_matches_oracle(dtype, tol):
+    """LBM_INIT_NEQ: f^eq plus (1 - 1/tau) times the first-order Chapman-Enskog part, on
+    random fields (gradients at every node including the ring), then 60 steps (f64)."""
+    nx, ny, tau = 37, 29, 0.9
+    r = uniform(2, (3, ny, nx))
+    rho, ux, uy = 1 + 0.01 * r[0], 0.05 * r[1], 0.05 * r[2]
+    p = O.Params(nx, ny, tau, 0.1)
+    ref0 = O.init_moments_neq(p, rho, ux, uy)
+    with make(nx, ny, tau, 0.1, dtype) as cav:
+        cav.set_moments(rho, ux, uy, neq=True)
+        f = cav.populations(host=True)
+        assert np.abs(f - O.to_soa(ref0)).max() < tol * 1.0
+        if dtype == "f64":
+            cav.step(60)
+            ref = O.to_soa(O.run(p, ref0, 60))
+            assert (np.abs(cav.populations(host=True) - ref) / ref).max() < 1e-12
+
+
 # ---------------------------------------------------------------- reductions and post-processing
 def test_residual_and_mass_match_oracle():
     nx, ny = 96, 64

@@ -250,3 +250,67 @@ def test_nee_mass_drift_is_small_and_reported():
     f = O.run(p, f0, 500)
     drift = (O.mass(p, f) - O.mass(p, f0)) / O.mass(p, f0)
     assert abs(drift) < 1e-2
+
+
+# ---------------------------------------------------------------- first-order non-equilibrium start
+def _quadratic_fields(nx, ny, seed):
+    rng = np.random.default_rng(seed)
+    X, Y = np.meshgrid(np.arange(nx, dtype=float), np.arange(ny, dtype=float))
+    a = rng.uniform(-1, 1, (2, 6)) * np.array([1e-2, 1e-2, 1e-4, 1e-4, 1e-4, 1e-2])
+
+    def quad(c):  # value and exact derivatives of c0 x + c1 y + c2 x^2 + c3 xy + c4 y^2 + c5
+        v = c[0] * X + c[1] * Y + c[2] * X * X + c[3] * X * Y + c[4] * Y * Y + c[5]
+        return v, c[0] + 2 * c[2] * X + c[3] * Y, c[1] + c[3] * X + 2 * c[4] * Y
+
+    ux, dxux, dyux = quad(a[0])
+    uy, dxuy, dyuy = quad(a[1])
+    rho = 1 + 0.01 * np.sin(0.3 * X + 0.2 * Y)
+    return rho, ux, uy, (dxux, dyux, dxuy, dyuy)
+
+
+def test_neq_start_keeps_the_moments():
+    """The non-equilibrium part carries no mass and no momentum: sum f = rho, sum c f = rho u."""
+    p = O.Params(13, 9, 0.7, 0.1)
+    rho, ux, uy, _ = _quadratic_fields(13, 9, 3)
+    f = O.init_moments_neq(p, rho, ux, uy)
+    assert np.abs(f.sum(-1) - rho).max() < 1e-14
+    assert np.abs((f * CX).sum(-1) - rho * ux).max() < 1e-14
+    assert np.abs((f * CY).sum(-1) - rho * uy).max() < 1e-14
+
+
+@pytest.mark.parametrize("tau", [0.55, 0.9, 1.7])
+def test_neq_start_stress_closed_form(tau):
+    """Second moment of the added part, from sum_j w_j c_a c_b c_c c_d = c_s^4 (three deltas):
+    Pi*_ab - Pi^eq_ab = -(tau - 1) rho c_s^2 (d_a u_b + d_b u_a), every node including the ring
+    (the one-sided end differences are exact for these quadratic fields)."""
+    nx, ny = 11, 14
+    p = O.Params(nx, ny, tau, 0.1)
+    rho, ux, uy, (dxux, dyux, dxuy, dyuy) = _quadratic_fields(nx, ny, 5)
+    d = O.init_moments_neq(p, rho, ux, uy) - O.init_moments(p, rho, ux, uy)
+    cs2 = 1.0 / 3.0
+    k = -(tau - 1) * rho * cs2
+    for pab, exact in (((d * CX * CX).sum(-1), k * 2 * dxux), ((d * CY * CY).sum(-1), k * 2 * dyuy),
+                       ((d * CX * CY).sum(-1), k * (dxuy + dyux))):
+        assert np.abs(pab - exact).max() < 1e-14 + 1e-11 * np.abs(exact).max()
+
+
+def _tg_start_error(neq, N=32, tau=1.2, U0=1e-3, t=6):
+    p = O.Params(N, N, tau, 0.0, mode=O.PERIODIC)
+    k = 2 * np.pi / N
+    X, Y = np.meshgrid(np.arange(N), np.arange(N))
+    ux = -U0 * np.cos(k * X) * np.sin(k * Y)
+    uy = U0 * np.sin(k * X) * np.cos(k * Y)
+    rho = 1 - 3 * U0 ** 2 / 4 * (np.cos(2 * k * X) + np.cos(2 * k * Y))
+    f = (O.init_moments_neq if neq else O.init_moments)(p, rho, ux, uy)
+    f = O.run(p, f, t)
+    nu = (tau - 0.5) / 3
+    inner = (slice(2, -2), slice(2, -2))  # away from the one-sided end differences
+    return np.abs(O.moments(p, f)[1] - ux * math.exp(-2 * nu * k * k * t))[inner].max() / U0
+
+
+def test_neq_start_removes_the_initial_layer():
+    """Taylor-Green vortex: started at equilibrium the populations first have to build their
+    stress, which perturbs u; started with the Chapman-Enskog stress, u follows the closed-form
+    decay from the first step.  A wrong sign or scale of the added part fails this."""
+    e_eq, e_neq = _tg_start_error(False), _tg_start_error(True)
+    assert e_neq < e_eq / 5, (e_eq, e_neq)
