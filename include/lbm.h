@@ -353,7 +353,8 @@ int lbm_net_get_grads(lbm_net *n, float *g);
 int lbm_net_zero_grads(lbm_net *n);
 /* out[3][H][W] = network(in[7][H][W]).  Asynchronous. */
 int lbm_net_forward(lbm_net *n, const float *in, int H, int W, float *out);
-/* Forward, loss = mean over masked pixels and 3 channels of (base + out - target)^2, backward:
+/* Forward, loss = mean over masked pixels and 3 channels of e^2, e = base + out - target with the
+ * masked mean of e removed in channel 0 (the density channel counts up to a constant), backward:
  * gradients are ADDED to the accumulated gradient (lbm_net_zero_grads clears it).  mask [H][W]
  * is 0/1; base, target [3][H][W].  *loss (host, may be NULL).  Synchronising. */
 int lbm_net_backward(lbm_net *n, const float *in, const float *base, const float *target,
@@ -377,6 +378,11 @@ int lbm_warm_input(const double *rho_c, const double *ux_c, const double *uy_c, 
  * unscaled -- ready for lbm_set_moments.  Asynchronous. */
 int lbm_warm_output(const float *in, const float *out, int nx, int ny, int H, double U, double *rho,
                     double *ux, double *uy, void *stream);
+/* Training target [3][H][nx] FP32 (DEVICE) from a fine steady solution (DEVICE [ny][nx] FP64):
+ * (rho - 1) * LBM_WARM_RHO_SCALE, ux / U, uy / U on rows < ny, zero on the padding rows.
+ * Asynchronous. */
+int lbm_warm_target(const double *rho, const double *ux, const double *uy, int nx, int ny, int H, double U,
+                    float *target, void *stream);
 
 /* The network's tensor-core product, exposed for tests and reuse: C[M][N] (op)= sum_k A[M][K]
  * B[N][K] with A, B bfloat16 (DEVICE, row-major, K contiguous; K, lda, ldb multiples of 8, 16-byte

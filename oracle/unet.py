@@ -146,8 +146,14 @@ def forward(params, w, x, rnd=False):
 
 
 def loss_and_grad(out, base, target, mask):
-    d = mask[None] * (base + out - target)
-    n = 3.0 * mask.sum()
+    """Masked mean squared error over the three channels, the density channel (0) compared up to
+    a constant: its masked mean error is removed first.  Returns (loss, dloss/dout); the mean's
+    own derivative cancels because the centred errors sum to zero."""
+    e = base + out - target
+    m = mask.sum()
+    e[0] = e[0] - (mask * e[0]).sum() / m
+    d = mask[None] * e
+    n = 3.0 * m
     return float((d * d).sum() / n), 2.0 * d / n
 
 

@@ -155,29 +155,46 @@ __global__ void k_up2_back(const float* __restrict__ dy, int C, int h, int w, fl
 }
 
 // Number of valid pixels (mask is 0/1) into cnt[0].
-__global__ void k_mask_count(const float* __restrict__ mask, long long P, double* cnt) {
-    __shared__ double sh[256];
-    double s = 0.0;
-    for (long long i = threadIdx.x; i < P; i += blockDim.x) s += mask[i];
-    sh[threadIdx.x] = s;
+// stats[0] = sum mask (the count n); stats[2] = sum mask (base + out - target)_0 / n, the mean
+// density-channel error, which the loss ignores (one block, fixed order).
+__global__ void k_mask_stats(const float* __restrict__ mask, const float* __restrict__ out, const float* __restrict__ base,
+                             const float* __restrict__ tgt, long long P, double* stats) {
+    __shared__ double sh[2][256];
+    double s = 0.0, e = 0.0;
+    for (long long i = threadIdx.x; i < P; i += blockDim.x) {
+        s += mask[i];
+        e += (double)(mask[i] * (base[i] + out[i] - tgt[i]));
+    }
+    sh[0][threadIdx.x] = s;
+    sh[1][threadIdx.x] = e;
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        if (threadIdx.x < o) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0) cnt[0] = sh[0];
+    if (threadIdx.x == 0) {
+        stats[0] = sh[0][0];
+        stats[2] = sh[0][0] > 0.0 ? sh[1][0] / sh[0][0] : 0.0;
+    }
 }
 
-// loss = sum mask (base + out - target)^2 / (3 cnt); dout = d loss / d out.  Partial sums per block.
+// loss = sum mask (e - [c = 0] mean_0)^2 / (3 n), e = base + out - target per channel c: the
+// density channel is compared up to a constant (the level of a steady density field only records
+// how long the wall scheme's mass loss acted; a uniform offset does not change the flow).
+// dout = d loss / d out (the mean's own derivative cancels).  Partial sums per block.
 __global__ void k_mse(const float* __restrict__ out, const float* __restrict__ base, const float* __restrict__ tgt,
-                      const float* __restrict__ mask, long long P, const double* __restrict__ cnt,
+                      const float* __restrict__ mask, long long P, const double* __restrict__ stats,
                       float* __restrict__ dout, double* __restrict__ part) {
     __shared__ double sh[256];
-    const float inv_n = (float)(1.0 / (3.0 * cnt[0]));
+    const float inv_n = (float)(1.0 / (3.0 * stats[0]));
+    const float mean0 = (float)stats[2];
     double s = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * P; i += (long long)gridDim.x * blockDim.x) {
         const float m = mask[i % P];
-        const float d = m * (base[i] + out[i] - tgt[i]);
+        const float d = m * (base[i] + out[i] - tgt[i] - (i < P ? mean0 : 0.f));
         dout[i] = 2.f * d * inv_n;
         s += (double)d * d;
     }
@@ -253,6 +270,18 @@ __global__ void k_warm_output(const float* __restrict__ in, const float* __restr
     rho[p] = 1.0 + (double)(in[p] + out[p]) / rho_s;
     ux[p] = (double)(in[P + p] + out[P + p]) * U;
     uy[p] = (double)(in[2 * P + p] + out[2 * P + p]) * U;
+}
+
+// training target: scaled fine fields, zero padding rows
+__global__ void k_warm_target(const double* __restrict__ rho, const double* __restrict__ ux, const double* __restrict__ uy,
+                              int nx, int ny, int H, double inv_u, float rho_s, float* __restrict__ t) {
+    const long long P = (long long)H * nx;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const bool in = p < (long long)nx * ny;
+    t[p] = in ? (float)((rho[p] - 1.0) * rho_s) : 0.f;
+    t[P + p] = in ? (float)(ux[p] * inv_u) : 0.f;
+    t[2 * P + p] = in ? (float)(uy[p] * inv_u) : 0.f;
 }
 
 }  // namespace nn
@@ -614,7 +643,7 @@ extern "C" int lbm_net_create(int width, unsigned long long seed, lbm_net** out)
     if (cudaMalloc(&n->params, off * 4) != cudaSuccess || cudaMalloc(&n->grads, off * 4) != cudaSuccess ||
         cudaMalloc(&n->adam_m, off * 4) != cudaSuccess || cudaMalloc(&n->adam_v, off * 4) != cudaSuccess ||
         cudaMalloc(&n->wq, q * 2) != cudaSuccess || cudaMalloc(&n->wf, f * 2) != cudaSuccess ||
-        cudaMalloc(&n->parts, 1024 * sizeof(double)) != cudaSuccess || cudaMalloc(&n->d_loss, 2 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&n->parts, 1024 * sizeof(double)) != cudaSuccess || cudaMalloc(&n->d_loss, 3 * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&n->d_err, sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&n->h_loss, sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
@@ -727,7 +756,7 @@ extern "C" int lbm_net_backward(lbm_net* n, const float* in, const float* base, 
     const long long P = (long long)H * W;
     const int nb = 512;
     // loss and dL/d(out) (into the dZ scratch, which backward copies before reusing it)
-    k_mask_count<<<1, 256, 0, n->stream>>>(mask, P, n->d_loss);
+    k_mask_stats<<<1, 256, 0, n->stream>>>(mask, n->act[g.out], base, target, P, n->d_loss);
     k_mse<<<nb, 256, 0, n->stream>>>(n->act[g.out], base, target, mask, P, n->d_loss, n->dz, n->parts);
     k_sum_parts<<<1, 32, 0, n->stream>>>(n->parts, nb, n->d_loss);
     rc = n->cuda(cudaGetLastError(), "loss");
@@ -790,6 +819,14 @@ extern "C" int lbm_warm_output(const float* in, const float* out, int nx, int ny
     if (!in || !out || !rho || !ux || !uy || H < ny) return LBM_EINVAL;
     k_warm_output<<<nblk((long long)nx * ny), 256, 0, (cudaStream_t)stream>>>(in, out, nx, ny, H, (float)U, LBM_WARM_RHO_SCALE,
                                                                             rho, ux, uy);
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
+
+extern "C" int lbm_warm_target(const double* rho, const double* ux, const double* uy, int nx, int ny, int H, double U,
+                               float* target, void* stream) {
+    if (!rho || !ux || !uy || !target || H < ny || nx < 1 || !(U != 0.0)) return LBM_EINVAL;
+    k_warm_target<<<nblk((long long)H * nx), 256, 0, (cudaStream_t)stream>>>(rho, ux, uy, nx, ny, H, 1.0 / U,
+                                                                           LBM_WARM_RHO_SCALE, target);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
 

@@ -164,3 +164,26 @@ def test_network_rejects_bad_shapes():
         assert e.value.code == B.LBM_EINVAL
     finally:
         B.lbm_net_destroy(n)
+
+
+def test_warm_target_and_output_roundtrip():
+    """lbm_warm_target scales a fine field (zero padding rows); lbm_warm_output with a zero
+    correction turns the same scaled channels back into the field."""
+    nx, ny, H, U0 = 48, 37, 48, 0.1
+    r = uniform(21, (3, ny, nx))
+    rho, ux, uy = 1 + 0.01 * r[0], 0.05 * r[1], 0.05 * r[2]
+    d = [torch.tensor(a, device="cuda") for a in (rho, ux, uy)]
+    t = torch.full((3, H, nx), 7.0, dtype=torch.float32, device="cuda")
+    B.lbm_warm_target(*d, nx, ny, H, U0, t)
+    torch.cuda.synchronize()
+    t_h = t.cpu().numpy()
+    exp = np.stack([(rho - 1) * B.LBM_WARM_RHO_SCALE, ux / U0, uy / U0]).astype(np.float32)
+    assert np.array_equal(t_h[:, :ny], exp) and not t_h[:, ny:].any()
+    inp = torch.zeros((7, H, nx), dtype=torch.float32, device="cuda")
+    inp[:3] = t
+    out = torch.zeros((3, H, nx), dtype=torch.float32, device="cuda")
+    f = [torch.empty((ny, nx), dtype=torch.float64, device="cuda") for _ in range(3)]
+    B.lbm_warm_output(inp, out, nx, ny, H, U0, *f)
+    torch.cuda.synchronize()
+    for got, ref in zip(f, (rho, ux, uy)):
+        assert np.abs(got.cpu().numpy() - ref).max() < 1e-8

@@ -98,3 +98,29 @@ def test_param_count_of_the_configured_width():
     """Width 20 gives the ~2M-parameter network (widths 20, 40, 80, 160, 160)."""
     n = sum(co * ci * 9 + co for ci, co in U.conv_list(20))
     assert 1.8e6 < n < 2.2e6
+
+
+def test_loss_ignores_the_density_level_only():
+    """The density channel is compared up to a constant, the velocity channels are not; the
+    returned dloss/dout matches central differences of the loss, element by element."""
+    rng = np.random.default_rng(8)
+    H, W = 6, 5
+    out, base, tgt = (rng.normal(size=(3, H, W)) for _ in range(3))
+    mask = (rng.uniform(size=(H, W)) > 0.3).astype(float)
+    loss, g = U.loss_and_grad(out, base, tgt, mask)
+    shifted = tgt.copy()
+    shifted[0] += 0.7
+    assert abs(U.loss_and_grad(out, base, shifted, mask)[0] - loss) < 1e-12
+    shifted = tgt.copy()
+    shifted[1] += 0.7
+    mean1 = (mask * (base[1] + out[1] - tgt[1])).sum() / mask.sum()
+    expect = (0.49 - 1.4 * mean1) / 3  # e_1 shifts by -0.7 over the masked pixels
+    assert abs(U.loss_and_grad(out, base, shifted, mask)[0] - loss - expect) < 1e-12
+    eps = 1e-6
+    for idx in [(0, 1, 1), (0, 4, 3), (1, 2, 0), (2, 5, 4), (0, 0, 0)]:
+        o = out.copy()
+        o[idx] += eps
+        lp = U.loss_and_grad(o, base, tgt, mask)[0]
+        o[idx] -= 2 * eps
+        lm = U.loss_and_grad(o, base, tgt, mask)[0]
+        assert abs((lp - lm) / (2 * eps) - g[idx]) < 1e-8
