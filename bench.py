@@ -151,9 +151,9 @@ def reference_arm(args, rank):
 
 
 # ------------------------------------------------------------------ our arm
-def read_profile_traffic():
-    """Per-launch DRAM bytes of the step kernel from the committed ncu summary, if it was taken
-    on the current kernel source."""
+def read_profile_traffic(shape: int):
+    """Per-launch DRAM bytes of the step kernel's launch shape `shape` from the committed ncu
+    summary, if it was taken on the current kernel source."""
     try:
         text = open(PROFILE).read()
     except OSError:
@@ -168,7 +168,7 @@ def read_profile_traffic():
     if vals.get("kernel_source_sha256_16") != digest:
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals[f"dram_bytes_per_launch_shape_{shape}"])
     except (KeyError, ValueError):
         return None
 
@@ -293,7 +293,7 @@ def our_arm(args, rank, world, local_rank):
     peak, peak_kind = measured_peak()
     algo_bytes = BYTES_PER_LU * NX * NY
     achieved = algo_bytes / step_kernel_s / 1e9
-    traffic = read_profile_traffic()
+    traffic = read_profile_traffic(cfg)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         import oracle as O

@@ -140,10 +140,12 @@ int lbm_launch_config_count(void);
 /* Select shape cfg in [0, lbm_launch_config_count()).  Synchronising.  LBM_EINVAL if out of range. */
 int lbm_set_launch_config(lbm_ctx *ctx, int cfg);
 
-/* Time every shape for steps_per_trial (>= 2) steps on a scratch context of the same size (the
- * caller's state is not touched; the scratch needs as much device memory as ctx) and select the
- * fastest.  *best / *best_glups (either may be NULL) receive the choice and its step rate in
- * 1e9 lattice updates per second.  Synchronising. */
+/* Time every shape on a scratch context of the same size (the caller's state is not touched; the
+ * scratch needs as much device memory as ctx): three rounds over all shapes of steps_per_trial
+ * (>= 2) plain steps and two checkpoint steps each, best time per shape, and select the shape
+ * with the lowest cost of a 100-step interval (99 plain + 1 checkpoint).  *best / *best_glups
+ * (either may be NULL) receive the choice and its step rate in 1e9 lattice updates per second.
+ * Synchronising. */
 int lbm_autotune(lbm_ctx *ctx, int steps_per_trial, int *best, double *best_glups);
 
 /* ------------------------------------------------------------------ observables */

@@ -3,22 +3,25 @@
 //
 //   C[M][N] (op)= sum_k A[M][K] * B[N][K]      (both K-contiguous; same contract as gemm_bf16_nt)
 //
-// CTA tile 128 x TN (TN = 32, 64 or 128, picked from N), K step 64 (four MMAs of K = 16), two
-// shared-memory stages; optional split-K over gridDim.z (atomic accumulation) and a transposed
-// store C[n][m], so a GEMM can put its long dimension (pixels) on the 128-row side.  Operands are
-// staged with cp.async into the canonical no-swizzle K-major layout (8 x 8 core matrices of 128
-// contiguous bytes; core matrices adjacent in K are 128 bytes apart, 8-row groups 1024 bytes
-// apart) and described to the tensor core by shared-memory descriptors.  One thread issues the
-// MMAs; tcgen05.commit arrives on the stage's mbarrier when they complete, which frees the stage
-// for the next load.  The 128 x TN FP32 accumulator lives in TN TMEM columns; each warp reads
-// its 32 lanes back with tcgen05.ld.  Every mbarrier wait is bounded (clock limit): on timeout
-// the CTA records an error, still frees its TMEM and returns.  Shared memory per CTA (two stages of
-// 16 KB + TN x 128 bytes) bounds residency so that the resident CTAs of one kernel never need more
-// than the 512 TMEM columns of an SM (3 x 128, 4 x 64, 5 x 32); no CTA waits on another while it
-// holds TMEM, so allocation can at worst wait for a neighbouring kernel's CTAs to finish.
+// CTA tile 128 x TN with TN = N rounded up to 16 (N <= 256; larger N is cut into equal tiles of at
+// most 256), K step 64.  Operand tiles arrive by TMA (cp.async.bulk.tensor, 128-byte swizzle,
+// out-of-range rows and K filled with zeros) into a ring of 2..6 shared-memory stages, each
+// guarded by a "full" mbarrier (TMA transaction bytes) and an "empty" mbarrier (tcgen05.commit of
+// the MMAs that read it).  Warp 0 lane 0 issues the copies, warp 1 lane 0 the MMAs (four K = 16
+// steps per stage, descriptors advanced 32 bytes inside the swizzle atom), warp 2 owns the TMEM
+// allocation; after the last commit every warp reads its 32 accumulator lanes back with
+// tcgen05.ld and stores them (row-major or transposed, store / accumulate / atomic add for
+// split-K over gridDim.z).  Shared memory per CTA is held under 110 KB so two CTAs share an SM
+// (one's epilogue overlaps the other's main loop) and their TMEM columns (<= 2 x 256) fit the
+// SM's 512.  Every mbarrier wait is bounded by a clock limit: on timeout the CTA records an error,
+// lets its issued copies and MMAs finish (bounded), frees its TMEM and returns.
+#include <cuda.h>          // CUtensorMap and the encoder's types; the encoder itself is fetched
+#include <cudaTypedefs.h>  // through the runtime's driver entry point (no link against libcuda)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <mutex>
 
 #include "lbm_nn_gemm.cuh"
 
@@ -27,88 +30,103 @@ namespace nn {
 
 namespace {
 
-constexpr int TM = 128, TK = 64, STAGES = 2;
-constexpr int kTileA = TM * TK * 2;  // 16 KB
+constexpr int TM = 128, TK = 64;
+constexpr int kTileA = TM * TK * 2;           // 16 KB
+constexpr int kSmemBudget = 110 * 1024;       // per CTA: two CTAs per SM
+constexpr int kSmemExtra = 1024 + 256;        // 1024-byte alignment slack + barriers / TMEM slot
 constexpr long long kWaitCycles = 2000000000ll;  // ~1 s
 
-template <int TN>
-struct Cfg {
-    static constexpr int kTileB = TN * TK * 2;
-    static constexpr int kStage = kTileA + kTileB;
-    static constexpr int kSmem = STAGES * kStage + 2048;  // + alignment slack, mbarriers, TMEM slot
-    // instruction descriptor, kind::f16: FP32 accumulate, BF16 A and B, both K-major, N, M
-    static constexpr uint32_t kIdesc =
-        (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+struct Plan {
+    int tn, tiles_n, cols, stages, smem;
 };
+
+Plan plan_for(int N) {
+    Plan p{};
+    p.tiles_n = (N + 255) / 256;
+    p.tn = ((N + p.tiles_n - 1) / p.tiles_n + 15) / 16 * 16;  // multiple of 16, <= 256
+    p.cols = 32;
+    while (p.cols < p.tn) p.cols <<= 1;  // TMEM allocation: a power of two >= 32
+    const int stage = kTileA + p.tn * TK * 2;
+    p.stages = (kSmemBudget - kSmemExtra) / stage;
+    if (p.stages > 6) p.stages = 6;
+    p.smem = p.stages * stage + kSmemExtra;
+    return p;
+}
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 
-__device__ __forceinline__ void cp16(uint32_t dst, const void* src, int bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes));
-}
-
-// shared-memory matrix descriptor: start >> 4, LBO >> 4, SBO >> 4, version 1, no swizzle
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// tcgen05 shared-memory descriptor, K-major operand in the 128-byte swizzle layout: start >> 4,
+// leading offset 16 B (unused by this layout), stride 1024 B between 8-row groups, version 1,
+// base offset 0 (stage tiles are 1024-aligned), layout type 2 = 128-byte swizzle.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFF);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)(16 >> 4) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
     d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
     return d;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait for the phase of the given parity; gives up early when another role aborted
+// (abort != nullptr) or after ~1 s.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort) {
     const long long t0 = clock64();
-    while (true) {
-        uint32_t done;
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
+    while (!mbar_test(bar, parity)) {
+        if ((abort && *abort) || clock64() - t0 > kWaitCycles) return false;
     }
+    return true;
 }
 
-// Stage rows [r0, r0 + ROWS) x K [k0, k0 + 64) of a K-contiguous matrix into the core-matrix
-// layout at s (row group stride 1024 bytes, K-chunk stride 128 bytes); zero outside [0,R) x [0,ke).
-template <int ROWS>
-__device__ __forceinline__ void stage_rows(uint32_t s, const __nv_bfloat16* X, int ld, int R, int ke, int r0, int k0) {
-    constexpr int PER = ROWS * 8 / 128;  // 16-byte chunks per thread
-#pragma unroll
-    for (int c = 0; c < PER; ++c) {
-        const int idx = threadIdx.x + c * 128;
-        const int r = idx >> 3, kc = idx & 7;
-        const uint32_t off = (uint32_t)((r >> 3) * 1024 + kc * 128 + (r & 7) * 16);
-        const int k = k0 + kc * 8;
-        const bool ok = (r0 + r) < R && k < ke;
-        cp16(s + off, ok ? (const void*)(X + (long long)(r0 + r) * ld + k) : (const void*)X, ok ? 16 : 0);
-    }
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
 }
 
-template <int TN>
-__global__ void __launch_bounds__(128, 1) k_gemm_umma(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int lda,
-                                                     const __nv_bfloat16* __restrict__ B, int ldb, float* __restrict__ C,
-                                                     int ldc, int op, int trans_c, int k_per_split, int* err) {
-    using CF = Cfg<TN>;
+__global__ void __launch_bounds__(128, 1)
+    k_gemm_tc05(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
+                float* __restrict__ C, int ldc, int op, int trans_c, int k_per_split, int tn, int cols, int stages,
+                int* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * CF::kStage);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + STAGES);
-    __shared__ int failed;
+    const int stage_bytes = kTileA + tn * TK * 2;
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + (size_t)stages * stage_bytes);
+    uint64_t* empty = full + stages;
+    uint64_t* done = empty + stages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    __shared__ volatile int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * tn;
     const int kb = blockIdx.z * k_per_split;
     const int ke = min(K, kb + k_per_split);
+    const int nk = ke > kb ? (ke - kb + TK - 1) / TK : 0;
+    auto sA = [&](int s) { return sa(base + (size_t)s * stage_bytes); };
+    auto sB = [&](int s) { return sa(base + (size_t)s * stage_bytes + kTileA); };
+
     if (threadIdx.x == 0) {
-        failed = 0;
-        for (int s = 0; s < STAGES; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sa(&bars[s])));
+        abort_flag = 0;
+        for (int s = 0; s < stages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sa(&full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sa(&empty[s])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sa(done)));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
     }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(sa(tmem_slot)), "r"((uint32_t)TN));
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(sa(tmem_slot)), "r"((uint32_t)cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
@@ -116,56 +134,58 @@ __global__ void __launch_bounds__(128, 1) k_gemm_umma(int M, int N, int K, const
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
     const uint32_t tmem = *tmem_slot;
 
-    const int nk = ke > kb ? (ke - kb + TK - 1) / TK : 0;
-    auto sA = [&](int s) { return sa(base + (size_t)s * CF::kStage); };
-    auto sB = [&](int s) { return sa(base + (size_t)s * CF::kStage + kTileA); };
-
-    if (nk > 0) {
-        stage_rows<TM>(sA(0), A, lda, M, ke, m0, kb);
-        stage_rows<TN>(sB(0), B, ldb, N, ke, n0, kb);
-        asm volatile("cp.async.commit_group;\n" ::);
-    }
-    for (int t = 0; t < nk; ++t) {
-        const int s = t & 1;
-        asm volatile("cp.async.wait_group 0;\n" ::);
-        asm volatile("fence.proxy.async.shared::cta;\n" ::);  // staged tile visible to the tensor core
-        __syncthreads();
-        if (threadIdx.x == 0 && !failed) {
+    if (warp == 0 && lane == 0) {
+        // producer: TMA copies of stage t % stages once the MMAs of t - stages released it
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+        int t = 0;
+        for (; t < nk; ++t) {
+            const int s = t % stages;
+            if (t >= stages && !mbar_wait(sa(&empty[s]), ((t / stages) - 1) & 1, &abort_flag)) {
+                abort_flag = 1;
+                break;
+            }
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(sa(&full[s])), "r"(stage_bytes)
+                         : "memory");
+            tma_load_2d(sA(s), &tmA, kb + t * TK, m0, sa(&full[s]));
+            tma_load_2d(sB(s), &tmB, kb + t * TK, n0, sa(&full[s]));
+        }
+        if (abort_flag)  // the copies already issued must land before the CTA may leave
+            for (int u = t > stages ? t - stages : 0; u < t; ++u) mbar_wait(sa(&full[u % stages]), (u / stages) & 1, nullptr);
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: four K = 16 steps per stage, accumulate after the first
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(tn >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+        for (int t = 0; t < nk; ++t) {
+            const int s = t % stages;
+            if (!mbar_wait(sa(&full[s]), (t / stages) & 1, &abort_flag)) {
+                abort_flag = 1;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
 #pragma unroll
             for (int kk = 0; kk < TK / 16; ++kk) {
-                const uint64_t da = smem_desc(sA(s) + kk * 256, 128, 1024);
-                const uint64_t db = smem_desc(sB(s) + kk * 256, 128, 1024);
+                const uint64_t da = desc_sw128(sA(s) + kk * 32);
+                const uint64_t db = desc_sw128(sB(s) + kk * 32);
                 const uint32_t acc = (t > 0 || kk > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(da), "l"(db), "r"(CF::kIdesc), "r"(acc));
+                    "l"(da), "l"(db), "r"(idesc), "r"(acc));
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(sa(&bars[s])));
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(sa(&empty[s])));
         }
-        if (t + 1 < nk) {
-            const int s2 = s ^ 1;
-            // the MMAs of tile t-1 read stage s2: wait for their commit before overwriting it
-            if (t >= 1 && !failed && !mbar_wait(sa(&bars[s2]), ((t - 1) >> 1) & 1)) failed = 1;
-            __syncthreads();
-            if (!failed) {
-                stage_rows<TM>(sA(s2), A, lda, M, ke, m0, kb + (t + 1) * TK);
-                stage_rows<TN>(sB(s2), B, ldb, N, ke, n0, kb + (t + 1) * TK);
-            }
-            asm volatile("cp.async.commit_group;\n" ::);
-        }
+        // arrives once every MMA issued above has completed (at once if none was issued)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(sa(done)));
     }
-    // all MMAs done: the last commit covers every earlier one of this thread
-    if (nk > 0 && !failed && !mbar_wait(sa(&bars[(nk - 1) & 1]), ((nk - 1) >> 1) & 1)) failed = 1;
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    __syncwarp();
 
-    if (!failed && nk > 0) {
-        // warp w owns TMEM lanes 32w .. 32w+31 = tile rows; 16 columns per load
+    // epilogue: warp w reads TMEM lanes 32w .. 32w+31 (= tile rows), 16 columns per load
+    const bool ok = mbar_wait(sa(done), 0, nullptr);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    if (ok && !abort_flag && nk > 0) {
         const int row = m0 + warp * 32 + lane;
 #pragma unroll 1
-        for (int c0 = 0; c0 < TN; c0 += 16) {
+        for (int c0 = 0; c0 < tn; c0 += 16) {
             uint32_t v[16];
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
             asm volatile(
@@ -192,29 +212,40 @@ __global__ void __launch_bounds__(128, 1) k_gemm_umma(int M, int N, int K, const
                 }
             }
         }
-    } else if (failed && threadIdx.x == 0) {
-        atomicExch(err, 1);
     }
+    if (threadIdx.x == 0 && (!ok || abort_flag)) atomicExch(err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((uint32_t)TN));
+    if (warp == 2) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((uint32_t)cols));
 }
 
-template <int TN>
-cudaError_t launch_umma(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, float* C,
-                        int ldc, GemmOp op, bool trans_c, int split_k, int* err, cudaStream_t st) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_umma<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<TN>::kSmem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    int kps = (K + split_k - 1) / split_k;
-    kps = (kps + TK - 1) / TK * TK;
-    split_k = (K + kps - 1) / kps;
-    dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, split_k);
-    k_gemm_umma<TN><<<grid, 128, Cfg<TN>::kSmem, st>>>(M, N, K, A, lda, B, ldb, C, ldc, (int)op, trans_c ? 1 : 0, kps, err);
-    return cudaGetLastError();
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Row-major [rows][K] bfloat16 (row stride ld elements) as a 2-D tensor {K, rows}, box {64, box_rows},
+// 128-byte swizzle, zero fill out of range.
+bool make_map(CUtensorMap* m, const __nv_bfloat16* X, int rows, int K, int ld, int box_rows) {
+    auto enc = encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(X), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
@@ -223,11 +254,25 @@ cudaError_t gemm_bf16_nt_umma(int M, int N, int K, const __nv_bfloat16* A, int l
                               float* C, int ldc, GemmOp op, bool trans_c, int split_k, int* err, cudaStream_t st) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if ((K & 7) || (lda & 7) || (ldb & 7) || K <= 0 || !err) return cudaErrorInvalidValue;
+    if (((uintptr_t)A & 15) || ((uintptr_t)B & 15)) return cudaErrorInvalidValue;  // TMA: 16-byte aligned bases
     if (split_k < 1) split_k = 1;
     if (split_k > 1 && op != kAtomicAdd) return cudaErrorInvalidValue;
-    if (N <= 32) return launch_umma<32>(M, N, K, A, lda, B, ldb, C, ldc, op, trans_c, split_k, err, st);
-    if (N <= 64) return launch_umma<64>(M, N, K, A, lda, B, ldb, C, ldc, op, trans_c, split_k, err, st);
-    return launch_umma<128>(M, N, K, A, lda, B, ldb, C, ldc, op, trans_c, split_k, err, st);
+    const Plan p = plan_for(N);
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A, M, K, lda, TM) || !make_map(&mb, B, N, K, ldb, p.tn)) return cudaErrorInvalidValue;
+    static int smem_set = 0;  // largest dynamic shared memory size opted in so far
+    if (p.smem > smem_set) {
+        const cudaError_t e = cudaFuncSetAttribute(k_gemm_tc05, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
+        if (e != cudaSuccess) return e;
+        smem_set = p.smem;
+    }
+    int kps = (K + split_k - 1) / split_k;
+    kps = (kps + TK - 1) / TK * TK;
+    split_k = (K + kps - 1) / kps;
+    const dim3 grid(p.tiles_n, (M + TM - 1) / TM, split_k);
+    k_gemm_tc05<<<grid, 128, p.smem, st>>>(ma, mb, M, N, K, C, ldc, (int)op, trans_c ? 1 : 0, kps, p.tn, p.cols,
+                                            p.stages, err);
+    return cudaGetLastError();
 }
 
 }  // namespace nn

@@ -191,10 +191,24 @@ def main(argv=None):
                               ("network_neq", lambda i: field_from(i, True), B.LBM_INIT_NEQ)):
         b, done, status, wall = batch_run(ec, a.dtype, a.tol, a.max_steps, init, flags)
         r_end, _ = B.lbm_batch_residual(b, len(ec))
+        if name == "rest":  # the converged fields judge the warm fields' velocity error
+            steady = [[t.cpu().numpy() for t in moments(b, i, NX, c[1])] for i, c in enumerate(ec)]
         B.lbm_batch_destroy(b)
         arms[name] = {"steps": done.tolist(), "status": status.tolist(), "wall_s": wall,
                       "total_steps": int(done.sum()), "converged": int((status == 1).sum()),
                       "final_residual": r_end.tolist()}
+    # relative L2 velocity error of the two warm fields against the converged run from rest
+    verr = {"coarse": [], "network": []}
+    for i in range(len(test)):
+        _, sx, sy = steady[i]
+        norm = np.sqrt((sx * sx + sy * sy).sum())
+        for k, use_net in (("coarse", False), ("network", True)):
+            f = field_from(i, use_net)
+            if f is None:
+                continue
+            wx, wy = f[1].cpu().numpy(), f[2].cpu().numpy()
+            verr[k].append(float(np.sqrt(((wx - sx) ** 2 + (wy - sy) ** 2).sum()) / norm))
+    report["velocity_error"] = {k: {"median": float(np.median(v)), "max": float(np.max(v))} for k, v in verr.items() if v}
     # steps ratio of each warm arm over rest; a draw whose warm run hit the cap counts at the cap
     rest = np.array(arms["rest"]["steps"], dtype=float)
     res_t = np.array([re for re, _ in test])
