@@ -380,6 +380,11 @@ int lbm_warm_input(const double *rho_c, const double *ux_c, const double *uy_c, 
  * unscaled -- ready for lbm_set_moments.  Asynchronous. */
 int lbm_warm_output(const float *in, const float *out, int nx, int ny, int H, double U, double *rho,
                     double *ux, double *uy, void *stream);
+/* Smooth a network output [3][H][W] (DEVICE) in place by `passes` 3x3 box-filter passes over rows
+ * [0, ny) (neighbourhoods clamped to those rows and the W columns; padding rows copied).  The
+ * warm start's convergence suffers from small-scale, non-solenoidal noise in the predicted
+ * correction more than from its smooth part.  scratch: DEVICE, 3 H W floats.  Asynchronous. */
+int lbm_warm_smooth(float *out, int ny, int H, int W, int passes, float *scratch, void *stream);
 /* Training target [3][H][nx] FP32 (DEVICE) from a fine steady solution (DEVICE [ny][nx] FP64):
  * (rho - 1) * LBM_WARM_RHO_SCALE, ux / U, uy / U on rows < ny, zero on the padding rows.
  * Asynchronous. */

@@ -112,6 +112,7 @@ _SIGS = [
     ("lbm_warm_input", _I, [_P, _P, _P, _I, _I, _D, _D, _D, _I, _I, _I, _P, _P]),
     ("lbm_warm_output", _I, [_P, _P, _I, _I, _I, _D, _P, _P, _P, _P]),
     ("lbm_warm_target", _I, [_P, _P, _P, _I, _I, _I, _D, _P, _P]),
+    ("lbm_warm_smooth", _I, [_P, _I, _I, _I, _I, _P, _P]),
     ("lbm_nn_gemm_bf16", _I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _I, _P]),
     ("lbm_nn_gemm_bf16_tc05", _I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _I, _I, _P, _P]),
     ("lbm_save", _I, [_P, ctypes.c_char_p]),
@@ -503,6 +504,12 @@ def lbm_warm_output(inp, out, nx, ny, H, U, rho, ux, uy, stream_handle=None) -> 
                                    stream_handle)
     if rc != LBM_OK:
         raise LBMError(rc, "lbm_warm_output")
+
+
+def lbm_warm_smooth(out, ny, H, W, passes, scratch, stream_handle=None) -> None:
+    rc = library().lbm_warm_smooth(_tptr(out), ny, H, W, int(passes), _tptr(scratch), stream_handle)
+    if rc != LBM_OK:
+        raise LBMError(rc, "lbm_warm_smooth")
 
 
 def lbm_warm_target(rho, ux, uy, nx, ny, H, U, target, stream_handle=None) -> None:

@@ -91,12 +91,14 @@ struct BatchArgs {
 };
 
 // Grid barrier with a bounded wait.  Returns false (and sets st->err) if the wait ran out or any
-// block reported a timeout; callers then return.
+// block reported a timeout; callers then return.  The block's writes reach thread 0 through the
+// block barrier, and thread 0's device-scope fence and release publish them (fences are
+// cumulative), so one fence per block suffices.
 __device__ __forceinline__ bool grid_barrier(BatchState* st, long long limit) {
     __shared__ int ok_sh;
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
+        __threadfence();
         int ok = 1;
         cuda::atomic_ref<unsigned, cuda::thread_scope_device> gen(st->bar_gen);
         cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(st->bar_count);

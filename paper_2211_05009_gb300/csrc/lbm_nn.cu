@@ -272,6 +272,27 @@ __global__ void k_warm_output(const float* __restrict__ in, const float* __restr
     uy[p] = (double)(in[2 * P + p] + out[2 * P + p]) * U;
 }
 
+// one 3x3 box-filter pass over the three correction channels, rows [0, ny) only, the
+// neighbourhood clamped to the valid rows and columns (replicate edges)
+__global__ void k_warm_smooth(const float* __restrict__ in, float* __restrict__ out, int ny, int H, int W) {
+    const long long P = (long long)H * W;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= 3 * P) return;
+    const int c = (int)(p / P), y = (int)((p % P) / W), x = (int)(p % W);
+    if (y >= ny) {
+        out[p] = in[p];
+        return;
+    }
+    const float* ch = in + (long long)c * P;
+    float s = 0.f;
+    for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int yy = min(max(y + dy, 0), ny - 1), xx = min(max(x + dx, 0), W - 1);
+            s += ch[(long long)yy * W + xx];
+        }
+    out[p] = s * (1.f / 9.f);
+}
+
 // training target: scaled fine fields, zero padding rows
 __global__ void k_warm_target(const double* __restrict__ rho, const double* __restrict__ ux, const double* __restrict__ uy,
                               int nx, int ny, int H, double inv_u, float rho_s, float* __restrict__ t) {
@@ -819,6 +840,18 @@ extern "C" int lbm_warm_output(const float* in, const float* out, int nx, int ny
     if (!in || !out || !rho || !ux || !uy || H < ny) return LBM_EINVAL;
     k_warm_output<<<nblk((long long)nx * ny), 256, 0, (cudaStream_t)stream>>>(in, out, nx, ny, H, (float)U, LBM_WARM_RHO_SCALE,
                                                                             rho, ux, uy);
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
+
+extern "C" int lbm_warm_smooth(float* out, int ny, int H, int W, int passes, float* scratch, void* stream) {
+    if (!out || !scratch || ny < 1 || H < ny || W < 1 || passes < 0) return LBM_EINVAL;
+    const long long n = 3ll * H * W;
+    for (int k = 0; k < passes; ++k) {
+        const float* src = (k & 1) ? scratch : out;
+        float* dst = (k & 1) ? out : scratch;
+        k_warm_smooth<<<nblk(n), 256, 0, (cudaStream_t)stream>>>(src, dst, ny, H, W);
+    }
+    if (passes & 1) cudaMemcpyAsync(out, scratch, n * sizeof(float), cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
 

@@ -325,10 +325,12 @@ __device__ __forceinline__ void step_row(const S* __restrict__ src, S* __restric
     unsigned pmask = 0;
     for (int q = 0; q < probes.n(); ++q)
         if (probes.py(q) == y && probes.px(q) >= x0 && probes.px(q) < x0 + V) pmask |= 1u << q;
-    // Per node.  EDGE = false: the whole segment is interior (no wall, lid or padding node), the
-    // case of all but the first and last lanes of a row, so the wall tests compile away; the
-    // arithmetic is the same either way.  Only 4- and 8-byte storage takes the split: for 16-bit
-    // storage the kernel is issue-bound and the second copy of the node code measured slower.
+    // Per node.  EDGE = false: every segment of the warp is interior (no wall, lid or padding
+    // node), the case of all but the first and last warps of a row, so the wall tests compile
+    // away; the arithmetic is the same either way.  The choice is made per warp (a per-lane choice
+    // would run both copies of the node code in a warp that holds a wall lane).  Only 4- and
+    // 8-byte storage takes the split: for 16-bit storage the kernel is issue-bound and the second
+    // copy of the node code measured slower.
     auto node = [&](auto edge_c, int i) {
         constexpr bool EDGE = decltype(edge_c)::value;
         const int x = x0 + i;
@@ -403,7 +405,7 @@ __device__ __forceinline__ void step_row(const S* __restrict__ src, S* __restric
             }
         }
     };
-    if (sizeof(S) < 4 || (y == 0) | (y == ny - 1) | (x0 == 0) | (x0 + V >= nx)) {
+    if (sizeof(S) < 4 || __any_sync(kFull, (y == 0) | (y == ny - 1) | (x0 == 0) | (x0 + V >= nx))) {
 #pragma unroll
         for (int i = 0; i < V; ++i) node(std::true_type{}, i);
     } else {

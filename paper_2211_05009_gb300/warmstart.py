@@ -3,13 +3,14 @@
   python -m paper_2211_05009_gb300.warmstart --train 256 --test 64 --epochs 30 --out net.bin
 
 1. Draws (Re, Ar) with Re ~ U[--re-min, --re-max], Ar ~ U[0.4, 2.0] (training seed 0, test seed 1).
-2. Coarse solutions: every draw on nxc x round(nxc Ar) nodes (nxc = nx / 4), run in one batch to
-   its Eq. 6 tolerance or a step cap.  The coarse grid cannot resolve high Re (tau -> 1/2), so the
-   coarse run uses Re_c = min(Re, --coarse-re-max); the network sees the true Re.
+2. Coarse solutions: every draw on nxc x round(nxc Ar) nodes (nxc = nx / --coarse-ratio), run in
+   one batch to its Eq. 6 tolerance or a step cap, at Re_c = min(Re, --coarse-re-max) (a coarse
+   grid cannot go to tau -> 1/2); the network sees the true Re.
 3. Training targets: the steady nx x round(nx Ar) fields of the training draws, from one batched
    run to --target-tol; draws that do not converge within the cap are excluded (and counted).
 4. Training: the network (lbm_net, BF16 tensor-core kernels) maps [coarse field on the fine grid,
    Re, Ar, masks] to a correction of the fine field; Adam, mini-batches by gradient accumulation.
+   At inference the correction is smoothed (--smooth box-filter passes, lbm_warm_smooth).
 5. Evaluation on the test draws, batched runs to --tol at equal residual: from rest (Sec. 2.2 i,
    the fallback and judge), from the interpolated coarse field and from the network's field, each
    of the two set either at equilibrium or with the first-order Chapman-Enskog stress of its
@@ -90,7 +91,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=256)
     ap.add_argument("--test", type=int, default=64)
-    ap.add_argument("--nx", type=int, default=128, help="fine grid width (coarse: nx / 4)")
+    ap.add_argument("--nx", type=int, default=128, help="fine grid width")
     ap.add_argument("--re-min", type=float, default=100.0)
     ap.add_argument("--re-max", type=float, default=1000.0)
     ap.add_argument("--width", type=int, default=20)
@@ -102,15 +103,17 @@ def main(argv=None):
     ap.add_argument("--target-tol", type=float, default=1e-9)
     ap.add_argument("--max-steps", type=int, default=400_000)
     ap.add_argument("--coarse-tol", type=float, default=1e-7)
-    ap.add_argument("--coarse-steps", type=int, default=100_000)
-    ap.add_argument("--coarse-re-max", type=float, default=400.0)
+    ap.add_argument("--coarse-steps", type=int, default=150_000)
+    ap.add_argument("--coarse-ratio", type=int, default=2, help="fine width / coarse width")
+    ap.add_argument("--coarse-re-max", type=float, default=1e9)
+    ap.add_argument("--smooth", type=int, default=4, help="box-filter passes over the network's correction")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     build()
     torch.manual_seed(0)
     st = torch.cuda.current_stream()
     report = {"args": vars(a)}
-    NX, NXC = a.nx, a.nx // 4
+    NX, NXC = a.nx, a.nx // a.coarse_ratio
     train, test = draws(a.train, 0, a.re_min, a.re_max), draws(a.test, 1, a.re_min, a.re_max)
     allp = train + test
 
@@ -179,6 +182,8 @@ def main(argv=None):
         out = torch.zeros((3, H, NX), dtype=torch.float32, device="cuda")
         if use_net:
             B.lbm_net_forward(net, inp, H, NX, out)
+            if a.smooth > 0:
+                B.lbm_warm_smooth(out, ny, H, NX, a.smooth, torch.empty_like(out), st.cuda_stream)
         f = [torch.empty((ny, nx), dtype=torch.float64, device="cuda") for _ in range(3)]
         B.lbm_warm_output(inp, out, nx, ny, H, U_LID, *f, st.cuda_stream)
         return f

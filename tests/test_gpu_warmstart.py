@@ -187,3 +187,27 @@ def test_warm_target_and_output_roundtrip():
     torch.cuda.synchronize()
     for got, ref in zip(f, (rho, ux, uy)):
         assert np.abs(got.cpu().numpy() - ref).max() < 1e-8
+
+
+def test_warm_smooth_matches_box_filter():
+    """lbm_warm_smooth: `passes` 3x3 means over rows [0, ny), indices clamped to those rows and the
+    columns; the padding rows are left as they were."""
+    H, W, ny, passes = 32, 40, 27, 3
+    a = uniform(31, (3, H, W)).astype(np.float32)
+    ref = a.astype(np.float64).copy()
+    for _ in range(passes):
+        v = ref[:, :ny]
+        yi = np.clip(np.arange(ny)[:, None] + np.array([-1, 0, 1])[None], 0, ny - 1)
+        xi = np.clip(np.arange(W)[:, None] + np.array([-1, 0, 1])[None], 0, W - 1)
+        acc = np.zeros_like(v)
+        for dy in range(3):
+            for dx in range(3):
+                acc += v[:, yi[:, dy]][:, :, xi[:, dx]]
+        ref[:, :ny] = acc / 9
+    t = torch.tensor(a, device="cuda")
+    scratch = torch.empty_like(t)
+    B.lbm_warm_smooth(t, ny, H, W, passes, scratch)
+    torch.cuda.synchronize()
+    got = t.cpu().numpy()
+    assert np.abs(got - ref).max() < 1e-6
+    assert np.array_equal(got[:, ny:], a[:, ny:])
