@@ -211,3 +211,24 @@ def test_warm_smooth_matches_box_filter():
     got = t.cpu().numpy()
     assert np.abs(got - ref).max() < 1e-6
     assert np.array_equal(got[:, ny:], a[:, ny:])
+
+
+def test_gemm_tcgen05_strided_operands_ignore_the_padding():
+    """Row strides larger than K (lda = K + 24, ldb = K + 8): the columns past K hold NaN and must
+    never be read (the tensor maps end at K and fill zeros)."""
+    M, N, K = 300, 72, 200
+    g = torch.Generator(device="cpu").manual_seed(5)
+    A = torch.full((M, K + 24), float("nan")).to(torch.bfloat16)
+    Bm = torch.full((N, K + 8), float("nan")).to(torch.bfloat16)
+    A[:, :K] = torch.randn(M, K, generator=g).to(torch.bfloat16)
+    Bm[:, :K] = torch.randn(N, K, generator=g).to(torch.bfloat16)
+    A, Bm = A.cuda(), Bm.cuda()
+    C = torch.zeros(M, N, dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert B.lbm_nn_gemm_bf16_tc05(M, N, K, A, K + 24, Bm, K + 8, C, N, 0, err, 0, 1) == B.LBM_OK
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    ref = A[:, :K].double().cpu().numpy() @ Bm[:, :K].double().cpu().numpy().T
+    got = C.cpu().numpy()
+    assert np.isfinite(got).all()
+    assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-5
