@@ -25,6 +25,7 @@ LBM_FLAG_LID_CORNERS_MOVING = 1
 LBM_MAX_PROBES = 4
 LBM_BATCH_SHAPES = 8
 LBM_INIT_NEQ = 1
+LBM_BATCH_MAX = 512
 RESIDUAL_INTERVAL = 100
 
 

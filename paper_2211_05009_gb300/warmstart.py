@@ -119,13 +119,22 @@ def main(argv=None):
 
     # 2. coarse solutions of every draw
     cc = [(NXC, max(3, round(NXC * ar)), min(re, a.coarse_re_max)) for re, ar in allp]
-    bc, done_c, stat_c, wall_c = batch_run(cc, a.dtype, a.coarse_tol, a.coarse_steps)
-    coarse = [moments(bc, i, c[0], c[1]) for i, c in enumerate(cc)]
-    B.lbm_batch_destroy(bc)
+    coarse, done_c, stat_c, wall_c = [], [], [], 0.0
+    for k0 in range(0, len(cc), B.LBM_BATCH_MAX):  # one batch holds at most LBM_BATCH_MAX cavities
+        part = cc[k0:k0 + B.LBM_BATCH_MAX]
+        bc, d, st_, w = batch_run(part, a.dtype, a.coarse_tol, a.coarse_steps)
+        coarse += [moments(bc, i, c[0], c[1]) for i, c in enumerate(part)]
+        B.lbm_batch_destroy(bc)
+        done_c += list(d)
+        stat_c += list(st_)
+        wall_c += w
+    done_c, stat_c = np.array(done_c), np.array(stat_c)
     report["coarse"] = {"wall_s": wall_c, "converged": int((stat_c == 1).sum()), "n": len(cc),
                         "lattice_updates": int(sum(c[0] * c[1] * d for c, d in zip(cc, done_c)))}
 
     # 3. training targets
+    if len(train) > B.LBM_BATCH_MAX:
+        raise SystemExit(f"--train {len(train)}: at most {B.LBM_BATCH_MAX} (one batch of targets)")
     tc = [(NX, round(NX * ar), re) for re, ar in train]
     bt, done_t, stat_t, wall_t = batch_run(tc, a.dtype, a.target_tol, a.max_steps)
     r_t, _ = B.lbm_batch_residual(bt, len(tc))
