@@ -17,7 +17,7 @@ constexpr int kStepConfigs = 6;
 // Fastest shape per storage type measured on GB300 at 2048 x 2048 (f64, f32, f32s, f16s, bf16s);
 // lbm_autotune re-measures on the caller's size.
 inline int default_step_config(int dtype) {
-    constexpr int k[5] = {1, 4, 0, 2, 2};  // fastest shapes of the 2048^2 sweep on GB300
+    constexpr int k[5] = {1, 4, 0, 2, 2};
     return (dtype >= 0 && dtype < 5) ? k[dtype] : 0;
 }
 
