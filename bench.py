@@ -298,7 +298,7 @@ def our_arm(args, rank, world, local_rank):
     if not args.no_cpu_baseline and world == 1:
         import oracle as O
         O.build()
-        steps_cpu = 16
+        steps_cpu = 64  # about 14 s of single-thread oracle work
         v, dt = oracle_sample(steps_cpu)
         cpu = {"value": v, "unit": "GLUPS", "cores": 1, "kind": "oracle",
                "sample": f"first {steps_cpu} time steps of the same 2048x2048 cavity ({dt:.1f} s, FP64, one thread)"}
