@@ -384,6 +384,7 @@ extern "C" int lbm_set_launch_config(lbm_ctx* c, int cfg) {
 }
 
 extern "C" int lbm_autotune(lbm_ctx* c, int steps_per_trial, int* best, double* best_glups) {
+    NvtxRange r("lbm_autotune");
     if (!c || steps_per_trial < 2) return c ? c->fail(LBM_EINVAL, "steps_per_trial < 2") : LBM_EINVAL;
     // trials run on a scratch context of the same shape so the caller's state is untouched
     void* (*sa)(size_t, void*) = g_alloc;
@@ -454,6 +455,7 @@ extern "C" int lbm_autotune(lbm_ctx* c, int steps_per_trial, int* best, double* 
 // ------------------------------------------------------------------ stepping
 extern "C" int lbm_step(lbm_ctx* c, long n) {
     if (!c) return LBM_EINVAL;
+    NvtxRange r("lbm_step");
     if (n < 0) return c->fail(LBM_EINVAL, "n < 0");
     return c->advance(n);
 }
@@ -479,6 +481,7 @@ extern "C" int lbm_residual(lbm_ctx* c, double* r) {
 }
 
 extern "C" int lbm_run_to_residual(lbm_ctx* c, double tol, long max_steps, long* steps_done) {
+    NvtxRange r("lbm_run_to_residual");
     if (!c || max_steps < 0 || !(tol >= 0)) return c ? c->fail(LBM_EINVAL, "bad tol/max_steps") : LBM_EINVAL;
     long long taken = 0;
     int rc = LBM_OK;
@@ -663,6 +666,7 @@ extern "C" int lbm_stream_function_window(lbm_ctx* c, int i0, int i1, int j0, in
 }
 
 extern "C" int lbm_stream_function(lbm_ctx* c, double* psi, double* psi_min, double* xc, double* yc) {
+    NvtxRange r("lbm_stream_function");
     if (!c) return LBM_EINVAL;
     const size_t bytes = (size_t)c->nx * c->ny * sizeof(double);
     double* dv = nullptr;

@@ -775,6 +775,7 @@ extern "C" int lbm_batch_set_stream(lbm_batch* b, void* stream) {
 
 extern "C" int lbm_batch_step(lbm_batch* b, long n) {
     if (!b) return LBM_EINVAL;
+    NvtxRange r("lbm_batch_step");
     if (n < 0) return b->fail(LBM_EINVAL, "n < 0");
     int rc = b->run(n, -1.0, 0);
     if (!rc) rc = b->pull_state();
@@ -783,6 +784,7 @@ extern "C" int lbm_batch_step(lbm_batch* b, long n) {
 
 extern "C" int lbm_batch_run_to_residual(lbm_batch* b, double tol, long max_steps, long* steps_done) {
     if (!b) return LBM_EINVAL;
+    NvtxRange r("lbm_batch_run_to_residual");
     if (!(tol > 0) || max_steps < 0) return b->fail(LBM_EINVAL, "need tol > 0 and max_steps >= 0");
     const long long start = b->step;
     const long long cap = start + max_steps;
@@ -933,6 +935,7 @@ extern "C" int lbm_batch_set_shape(lbm_batch* b, int shape) {
 
 extern "C" int lbm_batch_autotune(lbm_batch* b, int steps, int* chosen, float* ms) {
     if (!b) return LBM_EINVAL;
+    NvtxRange r("lbm_batch_autotune");
     if (steps < 1 || steps > 10000) return b->fail(LBM_EINVAL, "autotune: need 1 <= steps <= 10000");
     return b->autotune(steps, chosen, ms);
 }

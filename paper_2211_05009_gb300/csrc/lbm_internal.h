@@ -3,10 +3,19 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>  // header-only; the ranges cost nothing unless a profiler is attached
 
 #include "lbm_device.cuh"
 
 namespace lbm {
+
+// NVTX range over the host side of one library call (named in nsys / ncu timelines).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct StepGeometry {
     int grid_x, grid_y, blocks;

@@ -753,6 +753,7 @@ static int check_shape(lbm_net* n, int H, int W) {
 }
 
 extern "C" int lbm_net_forward(lbm_net* n, const float* in, int H, int W, float* out) {
+    NvtxRange nvtx_range("lbm_net_forward");
     if (!n || !in || !out) return LBM_EINVAL;
     int rc = check_shape(n, H, W);
     if (!rc) rc = forward(n, in, H, W);
@@ -769,6 +770,7 @@ extern "C" int lbm_net_forward(lbm_net* n, const float* in, int H, int W, float*
 
 extern "C" int lbm_net_backward(lbm_net* n, const float* in, const float* base, const float* target, const float* mask,
                                 int H, int W, double* loss) {
+    NvtxRange nvtx_range("lbm_net_backward");
     if (!n || !in || !base || !target || !mask) return LBM_EINVAL;
     int rc = check_shape(n, H, W);
     if (!rc) rc = forward(n, in, H, W);
@@ -790,6 +792,7 @@ extern "C" int lbm_net_backward(lbm_net* n, const float* in, const float* base, 
 }
 
 extern "C" int lbm_net_adam_step(lbm_net* n, float lr, float beta1, float beta2, float eps, float grad_scale) {
+    NvtxRange nvtx_range("lbm_net_adam_step");
     if (!n) return LBM_EINVAL;
     n->adam_t += 1;
     const float c1 = 1.f / (1.f - std::pow(beta1, (float)n->adam_t));
