@@ -331,7 +331,7 @@ int lbm_batch_set_barrier_limit(lbm_batch *b, double seconds, int absent_block);
 
 /* Not in the paper: a convolutional encoder-decoder that predicts an initial fine field for the
  * solver from (Re, Ar, a coarse field), to cut the steps to the Eq. 6 steady state; the plain run
- * from rest remains the fallback and the judge.  Architecture: 5 levels of two 3x3 convolutions
+ * from rest remains the fallback and the reference.  Architecture: 5 levels of two 3x3 convolutions
  * (widths w, 2w, 4w, 8w, 8w; leaky ReLU 0.1), 2x2 average pooling down, nearest x2 up with
  * skip concatenation, a 3x3 output head.  Input tensor [7][H][W] FP32 (see lbm_warm_input),
  * output [3][H][W]: corrections to input channels 0..2.  All convolutions run on BF16 tensor

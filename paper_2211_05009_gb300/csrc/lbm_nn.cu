@@ -1,7 +1,7 @@
 // lbm_nn.cu -- the learned warm start: a 5-level convolutional encoder-decoder (U-Net) that maps
 // (Re, Ar, a coarse steady field) to an initial fine rho/u field for the cavity solver, with its
 // training (forward, backward, Adam) written as CUDA kernels.  Not part of the paper; it serves
-// the time-to-steady-state of the method's runs (Eq. 6 criterion) and is judged by it.
+// the time-to-steady-state of the method's runs (Eq. 6 criterion) and is measured by it.
 //
 // Tensors are FP32 [C][H][W] (one sample).  Every 3x3 convolution (zero padding, stride 1) runs as
 // im2col + the BF16 tensor-core GEMM of lbm_nn_gemm.cu with FP32 accumulation:

@@ -12,7 +12,7 @@
    Re, Ar, masks] to a correction of the fine field; Adam, mini-batches by gradient accumulation.
    At inference the correction is smoothed (--smooth box-filter passes, lbm_warm_smooth).
 5. Evaluation on the test draws, batched runs to --tol at equal residual: from rest (Sec. 2.2 i,
-   the fallback and judge), from the interpolated coarse field and from the network's field, each
+   the fallback and the reference), from the interpolated coarse field and from the network's field, each
    of the two set either at equilibrium or with the first-order Chapman-Enskog stress of its
    velocity field (LBM_INIT_NEQ).  Reported: steps to the tolerance per draw, their totals and
    ratios (overall and by Re band), and wall times.
@@ -205,7 +205,7 @@ def main(argv=None):
                               ("network_neq", lambda i: field_from(i, True), B.LBM_INIT_NEQ)):
         b, done, status, wall = batch_run(ec, a.dtype, a.tol, a.max_steps, init, flags)
         r_end, _ = B.lbm_batch_residual(b, len(ec))
-        if name == "rest":  # the converged fields judge the warm fields' velocity error
+        if name == "rest":  # the converged fields measure the warm fields' velocity error
             steady = [[t.cpu().numpy() for t in moments(b, i, NX, c[1])] for i, c in enumerate(ec)]
         B.lbm_batch_destroy(b)
         arms[name] = {"steps": done.tolist(), "status": status.tolist(), "wall_s": wall,
