@@ -1,9 +1,9 @@
 // lbm_device.cuh -- device-side building blocks of the sm_103a D2Q9 cavity library.
 //
 // Method: Xiang & Shi (arXiv 2211.05009) Sec. 2.1 Eq. 1-3, Eq. 5 and Sec. 2.2 (i)-(iii).
-// Storage: SoA f[q][ny][pitch]; rows are 128-byte multiples and a warp owns 32*V consecutive
-// nodes of one row, so every population is read and written with one 16-byte vector access per
-// thread.  The +-1 x neighbours of a pull come from the adjacent lane by warp shuffle.
+// Storage: SoA f[q][ny][pitch]; rows are multiples of 512 bytes and a warp owns 32*V consecutive
+// nodes of one row, so every population is read and written with one 8- or 16-byte vector access
+// per thread.  The +-1 x neighbours of a pull come from the adjacent lane by warp shuffle.
 #pragma once
 
 #include <cuda_bf16.h>

@@ -21,7 +21,7 @@ constexpr Shape kShapes[kStepConfigs] = {{2, 2}, {1, 4}, {2, 2}, {4, 1}, {2, 4},
 
 StepGeometry step_geometry(int dtype, int cfg, int ny, long long pitch) {
     StepGeometry g{};
-    const int V = storage_bytes(dtype) == 8 ? 2 : 4;
+    const int V = storage_bytes(dtype) == 2 ? 4 : 2;  // as launch_step_cfg
     const Shape s = kShapes[cfg];
     g.grid_x = (int)(pitch / (32 * V));
     g.grid_y = (ny + s.BY * s.R - 1) / (s.BY * s.R);

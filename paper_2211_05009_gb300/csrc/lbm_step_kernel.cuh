@@ -14,8 +14,9 @@
 // the new snapshot: per node in the arithmetic type, per thread over its few nodes, and in FP64
 // from the warp level up (FP64 throughput on this part is a small fraction of FP32's).
 //
-// Thread mapping: blockDim = (32, BY); each lane owns V consecutive nodes (one 16-byte vector for
-// FP32/FP64, 8 bytes for 16-bit storage) of R consecutive rows, a warp 32*V nodes per row.  The
+// Thread mapping: blockDim = (32, BY); each lane owns V consecutive nodes (V = 2: a 16-byte vector
+// for FP64, 8 bytes for FP32; V = 4: 8 bytes for 16-bit storage) of R consecutive rows, a warp
+// 32*V nodes per row.  The
 // row pitch is a multiple of 32*V for every launch shape, so all vector accesses are in bounds;
 // padding nodes (x >= nx) store the rest state.
 #pragma once
@@ -493,7 +494,9 @@ static cudaError_t launch_step_shape(const StepArgs& a, bool reduce, cudaStream_
 // The shape tables; kShapes* in lbm_step.cu mirror them.
 template <typename S, bool SHIFTED>
 static cudaError_t launch_step_cfg(int cfg, const StepArgs& a, bool reduce, cudaStream_t st) {
-    constexpr int V = 16 / sizeof(S) < 4 ? 16 / sizeof(S) : 4;  // 2 for FP64, else 4
+    // nodes per lane: 2 for FP64 and FP32 storage (16- and 8-byte vectors; for FP32 the smaller
+    // register footprint buys more resident warps, measured faster than 4), 4 for 16-bit storage
+    constexpr int V = sizeof(S) == 2 ? 4 : 2;
     switch (cfg) {
         case 0: return launch_step_shape<S, SHIFTED, V, 2, 2, 0>(a, reduce, st);
         case 1: return launch_step_shape<S, SHIFTED, V, 1, 4, 0>(a, reduce, st);
