@@ -16,9 +16,8 @@
 //
 // Thread mapping: blockDim = (32, BY); each lane owns V consecutive nodes (V = 2: a 16-byte vector
 // for FP64, 8 bytes for FP32; V = 4: 8 bytes for 16-bit storage) of R consecutive rows, a warp
-// 32*V nodes per row.  The
-// row pitch is a multiple of 32*V for every launch shape, so all vector accesses are in bounds;
-// padding nodes (x >= nx) store the rest state.
+// 32*V nodes per row.  The row pitch is a multiple of 32*V for every launch shape, so all vector
+// accesses are in bounds; padding nodes (x >= nx) store the rest state.
 #pragma once
 
 #include <type_traits>
