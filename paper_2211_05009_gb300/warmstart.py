@@ -2,7 +2,8 @@
 
   python -m paper_2211_05009_gb300.warmstart --train 256 --test 64 --epochs 30 --out net.bin
 
-1. Draws (Re, Ar) with Re ~ U[--re-min, --re-max], Ar ~ U[0.4, 2.0] (training seed 0, test seed 1).
+1. Draws (Re, Ar) with Re ~ U[--re-min, --re-max], Ar ~ U[0.4, 2.0] (training seed 0, test seed 1,
+   validation seed 2).
 2. Coarse solutions: every draw on nxc x round(nxc Ar) nodes (nxc = nx / --coarse-ratio), run in
    one batch to its Eq. 6 tolerance or a step cap, at Re_c = min(Re, --coarse-re-max) (a coarse
    grid cannot go to tau -> 1/2); the network sees the true Re.
@@ -11,11 +12,14 @@
 4. Training: the network (lbm_net, BF16 tensor-core kernels) maps [coarse field on the fine grid,
    Re, Ar, masks] to a correction of the fine field; Adam, mini-batches by gradient accumulation.
    At inference the correction is smoothed (--smooth box-filter passes, lbm_warm_smooth).
-5. Evaluation on the test draws, batched runs to --tol at equal residual: from rest (Sec. 2.2 i,
-   the fallback and the reference), from the interpolated coarse field and from the network's field, each
-   of the two set either at equilibrium or with the first-order Chapman-Enskog stress of its
-   velocity field (LBM_INIT_NEQ).  Reported: steps to the tolerance per draw, their totals and
-   ratios (overall and by Re band), and wall times.
+5. Fallback gate: on the validation draws, runs from rest and from the network's field pick the
+   Reynolds number below which the warm start pays (least total steps); above it the solver
+   starts from rest.
+6. Evaluation on the test draws, batched runs to --tol at equal residual: from rest (Sec. 2.2 i,
+   the fallback and the reference), from the interpolated coarse field and from the network's
+   field, each set either at equilibrium or with the first-order Chapman-Enskog stress of its
+   velocity field (LBM_INIT_NEQ), and the gated policy.  Reported: steps to the tolerance per
+   draw, their totals and ratios (overall and by Re band), and wall times.
 Prints one JSON document.
 """
 from __future__ import annotations
@@ -91,6 +95,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=256)
     ap.add_argument("--test", type=int, default=64)
+    ap.add_argument("--val", type=int, default=48, help="validation draws that choose the fallback gate")
     ap.add_argument("--nx", type=int, default=128, help="fine grid width")
     ap.add_argument("--re-min", type=float, default=100.0)
     ap.add_argument("--re-max", type=float, default=1000.0)
@@ -115,7 +120,8 @@ def main(argv=None):
     report = {"args": vars(a)}
     NX, NXC = a.nx, a.nx // a.coarse_ratio
     train, test = draws(a.train, 0, a.re_min, a.re_max), draws(a.test, 1, a.re_min, a.re_max)
-    allp = train + test
+    val = draws(a.val, 2, a.re_min, a.re_max)
+    allp = train + test + val
 
     # 2. coarse solutions of every draw
     cc = [(NXC, max(3, round(NXC * ar)), min(re, a.coarse_re_max)) for re, ar in allp]
@@ -177,32 +183,54 @@ def main(argv=None):
     if a.out:
         B.lbm_net_save(net, a.out)
 
-    # 5. evaluation: rest vs interpolated coarse vs network, all to the same tolerance
-    ec = [(NX, round(NX * ar), re) for re, ar in test]
-    off = len(train)
-    inputs = [make_input(coarse[off + i], re, ar, NX, ec[i][1]) for i, (re, ar) in enumerate(test)]
+    def evaluator(dset, off):
+        """Cases, network inputs and warm-field builder of a draw set whose coarse runs start at off."""
+        cases = [(NX, round(NX * ar), re) for re, ar in dset]
+        inps = [make_input(coarse[off + i], re, ar, NX, cases[i][1]) for i, (re, ar) in enumerate(dset)]
 
-    def field_from(i, use_net):
-        """(rho, ux, uy) of a warm start; None (start from rest) if the coarse run went non-finite."""
-        nx, ny = NX, ec[i][1]
-        if stat_c[off + i] == 3:
-            return None
-        inp, H = inputs[i]
-        out = torch.zeros((3, H, NX), dtype=torch.float32, device="cuda")
-        if use_net:
-            B.lbm_net_forward(net, inp, H, NX, out)
-            if a.smooth > 0:
-                B.lbm_warm_smooth(out, ny, H, NX, a.smooth, torch.empty_like(out), st.cuda_stream)
-        f = [torch.empty((ny, nx), dtype=torch.float64, device="cuda") for _ in range(3)]
-        B.lbm_warm_output(inp, out, nx, ny, H, U_LID, *f, st.cuda_stream)
-        return f
+        def field(i, use_net):
+            """(rho, ux, uy) of a warm start; None (start from rest) if the coarse run went non-finite."""
+            nx, ny = NX, cases[i][1]
+            if stat_c[off + i] == 3:
+                return None
+            inp, H = inps[i]
+            out = torch.zeros((3, H, NX), dtype=torch.float32, device="cuda")
+            if use_net:
+                B.lbm_net_forward(net, inp, H, NX, out)
+                if a.smooth > 0:
+                    B.lbm_warm_smooth(out, ny, H, NX, a.smooth, torch.empty_like(out), st.cuda_stream)
+            f = [torch.empty((ny, nx), dtype=torch.float64, device="cuda") for _ in range(3)]
+            B.lbm_warm_output(inp, out, nx, ny, H, U_LID, *f, st.cuda_stream)
+            return f
+        return cases, field
 
+    # 5. fallback gate from the validation draws
+    gate = None
+    if val:
+        vc, vfield = evaluator(val, len(train) + len(test))
+        bv, v_rest, _, _ = batch_run(vc, a.dtype, a.tol, a.max_steps)
+        B.lbm_batch_destroy(bv)
+        bv, v_net, _, _ = batch_run(vc, a.dtype, a.tol, a.max_steps, lambda i: vfield(i, True), B.LBM_INIT_NEQ)
+        B.lbm_batch_destroy(bv)
+        v_re = np.array([re for re, _ in val])
+        cands = sorted(set(v_re.tolist())) + [a.re_max + 1.0]
+        totals = [float(np.where(v_re < g, v_net, v_rest).sum()) for g in cands]
+        gate = cands[int(np.argmin(totals))]
+        report["gate"] = {"re_gate": gate, "val_total_rest": int(v_rest.sum()), "val_total_network": int(v_net.sum()),
+                          "val_total_gated": int(min(totals)), "n_val": len(val)}
+
+    # 6. evaluation: rest vs interpolated coarse vs network, all to the same tolerance
+    ec, field_from = evaluator(test, len(train))
+    res_t = np.array([re for re, _ in test])
+    arm_list = [("rest", None, 0),
+                ("coarse", lambda i: field_from(i, False), 0),
+                ("coarse_neq", lambda i: field_from(i, False), B.LBM_INIT_NEQ),
+                ("network", lambda i: field_from(i, True), 0),
+                ("network_neq", lambda i: field_from(i, True), B.LBM_INIT_NEQ)]
+    if gate is not None:
+        arm_list.append(("network_gated", lambda i: field_from(i, True) if res_t[i] < gate else None, B.LBM_INIT_NEQ))
     arms = {}
-    for name, init, flags in (("rest", None, 0),
-                              ("coarse", lambda i: field_from(i, False), 0),
-                              ("coarse_neq", lambda i: field_from(i, False), B.LBM_INIT_NEQ),
-                              ("network", lambda i: field_from(i, True), 0),
-                              ("network_neq", lambda i: field_from(i, True), B.LBM_INIT_NEQ)):
+    for name, init, flags in arm_list:
         b, done, status, wall = batch_run(ec, a.dtype, a.tol, a.max_steps, init, flags)
         r_end, _ = B.lbm_batch_residual(b, len(ec))
         if name == "rest":  # the converged fields measure the warm fields' velocity error
@@ -225,13 +253,12 @@ def main(argv=None):
     report["velocity_error"] = {k: {"median": float(np.median(v)), "max": float(np.max(v))} for k, v in verr.items() if v}
     # steps ratio of each warm arm over rest; a draw whose warm run hit the cap counts at the cap
     rest = np.array(arms["rest"]["steps"], dtype=float)
-    res_t = np.array([re for re, _ in test])
     ev = {"n": len(test), "rest_converged": arms["rest"]["converged"],
           "total_steps": {k: v["total_steps"] for k, v in arms.items()},
           "wall_s": {k: v["wall_s"] for k, v in arms.items()},
           "converged": {k: v["converged"] for k, v in arms.items()}, "ratio_over_rest": {}}
     ok = np.array(arms["rest"]["status"]) == 1
-    for k in ("coarse", "coarse_neq", "network", "network_neq"):
+    for k in [n for n in arms if n != "rest"]:
         r = np.array(arms[k]["steps"], dtype=float)[ok] / rest[ok]
         band = {}
         for lo, hi in ((0, 400), (400, 700), (700, 1e9)):
