@@ -43,6 +43,20 @@ def draws(n, seed, re_min, re_max):
     return [(float(rng.uniform(re_min, re_max)), float(rng.uniform(0.4, 2.0))) for _ in range(n)]
 
 
+def choose_gate(re, steps_rest, steps_warm, re_cap):
+    """Fallback gate: the Reynolds number g minimising the total steps of the policy 'warm start
+    if Re < g, else start from rest' on the given draws (candidates: every draw's Re and re_cap,
+    which means warm everywhere).  Ties go to the smallest g (the most draws start from rest).
+    Returns (g, total steps at g)."""
+    re = np.asarray(re, dtype=float)
+    rest = np.asarray(steps_rest, dtype=float)
+    warm = np.asarray(steps_warm, dtype=float)
+    cands = sorted(set(re.tolist())) + [float(re_cap)]
+    totals = [float(np.where(re < g, warm, rest).sum()) for g in cands]
+    k = int(np.argmin(totals))
+    return cands[k], totals[k]
+
+
 def pad16(n):
     return (n + 15) // 16 * 16
 
@@ -212,12 +226,9 @@ def main(argv=None):
         B.lbm_batch_destroy(bv)
         bv, v_net, _, _ = batch_run(vc, a.dtype, a.tol, a.max_steps, lambda i: vfield(i, True), B.LBM_INIT_NEQ)
         B.lbm_batch_destroy(bv)
-        v_re = np.array([re for re, _ in val])
-        cands = sorted(set(v_re.tolist())) + [a.re_max + 1.0]
-        totals = [float(np.where(v_re < g, v_net, v_rest).sum()) for g in cands]
-        gate = cands[int(np.argmin(totals))]
+        gate, total = choose_gate([re for re, _ in val], v_rest, v_net, a.re_max + 1.0)
         report["gate"] = {"re_gate": gate, "val_total_rest": int(v_rest.sum()), "val_total_network": int(v_net.sum()),
-                          "val_total_gated": int(min(totals)), "n_val": len(val)}
+                          "val_total_gated": int(total), "n_val": len(val)}
 
     # 6. evaluation: rest vs interpolated coarse vs network, all to the same tolerance
     ec, field_from = evaluator(test, len(train))
