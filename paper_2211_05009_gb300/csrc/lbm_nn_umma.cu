@@ -260,11 +260,20 @@ cudaError_t gemm_bf16_nt_umma(int M, int N, int K, const __nv_bfloat16* A, int l
     const Plan p = plan_for(N);
     CUtensorMap ma, mb;
     if (!make_map(&ma, A, M, K, lda, TM) || !make_map(&mb, B, N, K, ldb, p.tn)) return cudaErrorInvalidValue;
-    static int smem_set = 0;  // largest dynamic shared memory size opted in so far
-    if (p.smem > smem_set) {
-        const cudaError_t e = cudaFuncSetAttribute(k_gemm_tc05, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
+    {
+        // opt in to the plan's dynamic shared memory: the attribute belongs to the current device,
+        // so the largest size set so far is kept per device (thread-safe)
+        static std::mutex mu;
+        static int opted[64] = {};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
-        smem_set = p.smem;
+        std::lock_guard<std::mutex> lock(mu);
+        if (dev >= 64 || p.smem > opted[dev]) {
+            e = cudaFuncSetAttribute(k_gemm_tc05, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
+            if (e != cudaSuccess) return e;
+            if (dev < 64) opted[dev] = p.smem;
+        }
     }
     int kps = (K + split_k - 1) / split_k;
     kps = (kps + TK - 1) / TK * TK;
