@@ -359,11 +359,13 @@ __device__ __forceinline__ void step_row(const S* __restrict__ src, S* __restric
             // BGK as an increment d_j = (f^eq_j - f_j)/tau added to the pulled value.  The
             // increment must carry no momentum; in FP32 the rounding of f^eq breaks that by a
             // few ulps in the same direction every step, so the x and y momentum of d is
-            // removed from the (1,3) and (2,4) pairs (a rounding-level change).
+            // removed from the (1,3) and (2,4) pairs (a rounding-level change).  With 16-bit
+            // storage the stored rounding (~1e-3 relative) swamps that drift, and the kernel is
+            // issue-bound, so the correction is made for FP32 storage only.
             C d[9];
 #pragma unroll
             for (int j = 0; j < 9; ++j) d[j] = omega * (e[j] - g[j]);
-            if constexpr (sizeof(C) == 4) {
+            if constexpr (sizeof(C) == 4 && sizeof(S) == 4) {
                 const C mx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
                 const C my = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
                 d[1] -= C(0.5) * mx;
