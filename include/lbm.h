@@ -89,6 +89,12 @@ typedef struct {
  * LBM_ENOMEM, LBM_ECUDA.  On failure *out is NULL and lbm_last_error(NULL) holds the reason. */
 int lbm_create(int nx, int ny, double Re, double U_lid, lbm_dtype dtype, lbm_ctx **out);
 
+/* As lbm_create, with LBM_FLAG_* flags.  The library turns Re into tau exactly as lbm_create does
+ * (Re = U L / nu with L = nx, Sec. 1; tau = 3 nu + 1/2, Eq. 5), so a caller that wants a flag
+ * still never computes tau.  Errors: those of lbm_create, and LBM_EINVAL for an unknown flag. */
+int lbm_create_flags(int nx, int ny, double Re, double U_lid, lbm_dtype dtype, unsigned flags,
+                     lbm_ctx **out);
+
 /* As lbm_create with tau given directly and LBM_FLAG_* flags. */
 int lbm_create_ex(int nx, int ny, double tau, double U_lid, lbm_dtype dtype, unsigned flags,
                   lbm_ctx **out);
@@ -222,14 +228,17 @@ int lbm_probe_clear(lbm_ctx *ctx);
  *           the host and no host synchronisation happens.
  * Scratch: a fixed device array of LBM_STATIC_SCRATCH_DOUBLES doubles (4 MiB), defined in the
  * library and held by every GPU that loads it until the process exits.  A call needs
- * nx*ceil(ny/32) + 2*ceil(ny/32)*ceil(nx/128) doubles of it (a 4096 x 4000 grid fits); larger
+ * nx*ceil(ny/32) + 2*ceil(ny/32)*ceil(nx/128) doubles of it (a 4096 x 4000 grid fits), and
+ * ceil(ny/32) may not exceed 65535 (ny <= 2,097,120; one launch row per 32-row segment); other
  * grids return LBM_ETOOBIG without launching anything.  Every element a call reads it has
  * written first, so nothing needs to be cleared between calls; but all calls share the one
  * array, so calls that can overlap on the GPU (other streams, other host threads) race and
  * must be ordered by the caller.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first call before any
  * stream capture.  Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
- * Errors: LBM_EINVAL (NULL ux/result, nx or ny < 1), LBM_ETOOBIG, LBM_ECUDA. */
+ * Errors: LBM_EINVAL (NULL ux/result, nx or ny < 1), LBM_ETOOBIG, LBM_ECUDA.  A CUDA error
+ * that an earlier, unrelated call left pending is reported as LBM_ECUDA before anything is
+ * launched and is left pending for its owner; an error of this call's own launches is cleared. */
 #define LBM_STATIC_SCRATCH_DOUBLES (1 << 19)
 int lbm_stream_function_static(const double *ux, int nx, int ny, double *psi, double *result,
                                void *stream);

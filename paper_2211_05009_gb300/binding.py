@@ -51,6 +51,7 @@ _lib = None
 _D, _I, _L, _P, _DP = ctypes.c_double, ctypes.c_int, ctypes.c_long, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
 _SIGS = [
     ("lbm_create", _I, [_I, _I, _D, _D, _I, ctypes.POINTER(_P)]),
+    ("lbm_create_flags", _I, [_I, _I, _D, _D, _I, ctypes.c_uint, ctypes.POINTER(_P)]),
     ("lbm_create_ex", _I, [_I, _I, _D, _D, _I, ctypes.c_uint, ctypes.POINTER(_P)]),
     ("lbm_destroy", None, [_P]),
     ("lbm_last_error", ctypes.c_char_p, [_P]),
@@ -164,6 +165,13 @@ def _check(ctx, rc: int):
 def lbm_create(nx: int, ny: int, Re: float, U_lid: float, dtype: str | int = "f32s"):
     out = ctypes.c_void_p()
     rc = library().lbm_create(nx, ny, Re, U_lid, DTYPES.get(dtype, dtype), ctypes.byref(out))
+    _check(None, rc)
+    return out.value
+
+
+def lbm_create_flags(nx: int, ny: int, Re: float, U_lid: float, dtype: str | int = "f32s", flags: int = 0):
+    out = ctypes.c_void_p()
+    rc = library().lbm_create_flags(nx, ny, Re, U_lid, DTYPES.get(dtype, dtype), flags, ctypes.byref(out))
     _check(None, rc)
     return out.value
 

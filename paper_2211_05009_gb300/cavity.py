@@ -22,12 +22,10 @@ class Cavity:
                  tau: float | None = None, corners_moving: bool = False, stream: torch.cuda.Stream | None = None):
         if (Re is None) == (tau is None):
             raise ValueError("give exactly one of Re and tau")
-        if Re is not None and not corners_moving:
-            self.ctx = B.lbm_create(nx, ny, Re, U, dtype)
+        flags = B.LBM_FLAG_LID_CORNERS_MOVING if corners_moving else 0
+        if Re is not None:
+            self.ctx = B.lbm_create_flags(nx, ny, Re, U, dtype, flags)
         else:
-            if tau is None:
-                tau = 3.0 * U * nx / Re + 0.5
-            flags = B.LBM_FLAG_LID_CORNERS_MOVING if corners_moving else 0
             self.ctx = B.lbm_create_ex(nx, ny, tau, U, dtype, flags)
         self.nx, self.ny, self.dtype = nx, ny, dtype
         self.stream = stream if stream is not None else torch.cuda.current_stream()

@@ -329,7 +329,8 @@ extern "C" int lbm_create_ex(int nx, int ny, double tau, double U, lbm_dtype dty
     return LBM_OK;
 }
 
-extern "C" int lbm_create(int nx, int ny, double Re, double U, lbm_dtype dtype, lbm_ctx** out) {
+extern "C" int lbm_create_flags(int nx, int ny, double Re, double U, lbm_dtype dtype, unsigned flags,
+                                lbm_ctx** out) {
     if (!(Re > 0.0) || !std::isfinite(Re)) {
         g_create_error = fmt("Re = %g: need Re > 0", Re);
         if (out) *out = nullptr;
@@ -337,7 +338,11 @@ extern "C" int lbm_create(int nx, int ny, double Re, double U, lbm_dtype dtype, 
     }
     const double nu = U * nx / Re;  // Re = U L / nu with L = nx
     const double tau = 3.0 * nu + 0.5;  // Eq. 5 with c_s^2 = 1/3, dt = 1
-    return lbm_create_ex(nx, ny, tau, U, dtype, 0u, out);
+    return lbm_create_ex(nx, ny, tau, U, dtype, flags, out);
+}
+
+extern "C" int lbm_create(int nx, int ny, double Re, double U, lbm_dtype dtype, lbm_ctx** out) {
+    return lbm_create_flags(nx, ny, Re, U, dtype, 0u, out);
 }
 
 extern "C" const char* lbm_last_error(const lbm_ctx* c) {

@@ -53,7 +53,21 @@ def test_invalid_arguments_rejected_without_device(lib):
     assert L.lbm_create_ex(10, 10, 0.5, 0.1, 2, 0, ctypes.byref(out)) == B.LBM_EINVAL
     assert L.lbm_create_ex(10, 10, 0.8, 0.1, 9, 0, ctypes.byref(out)) == B.LBM_EINVAL
     assert L.lbm_create(10, 10, -5.0, 0.1, 2, ctypes.byref(out)) == B.LBM_EINVAL
+    assert L.lbm_create_flags(10, 10, 0.0, 0.1, 2, 1, ctypes.byref(out)) == B.LBM_EINVAL
+    assert "Re" in B.lbm_last_error(None)
+    assert L.lbm_create_flags(10, 10, 100.0, 0.1, 2, 2, ctypes.byref(out)) == B.LBM_EINVAL
+    assert "flags" in B.lbm_last_error(None)
     assert out.value is None
+
+
+def test_python_package_does_no_method_arithmetic():
+    """Re -> nu -> tau (Eq. 5) happens in the library only: no Python module of the package
+    spells the relation between Re, nu and tau."""
+    pkg = os.path.join(ROOT, "paper_2211_05009_gb300")
+    for path in glob.glob(os.path.join(pkg, "*.py")):
+        code = "\n".join(l.split("#")[0] for l in open(path).read().splitlines())
+        assert not re.search(r"\b(tau|nu)\s*=[^=].*\b(Re|re)\b", code), path
+        assert not re.search(r"\+\s*0\.5\b", code), path
 
 
 def test_create_without_gpu_fails_loudly(lib):

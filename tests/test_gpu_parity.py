@@ -39,6 +39,20 @@ def make(nx, ny, tau, U, dtype, corners=False):
     return Cavity(nx, ny, tau=tau, U=U, dtype=dtype, corners_moving=corners)
 
 
+def test_create_flags_takes_re_in_the_library():
+    """lbm_create_flags(Re, LBM_FLAG_LID_CORNERS_MOVING): tau from Re in the library (Eq. 5,
+    L = nx), populations equal the oracle's run of the same Re with moving lid corners."""
+    nx, ny, Re, U, steps = 129, 40, 80.0, 0.1, 300
+    p = O.Params.from_re(nx, ny, Re, U, corner_moving=True)
+    with Cavity(nx, ny, Re=Re, U=U, dtype="f64", corners_moving=True) as cav:
+        assert cav.info.flags == B.LBM_FLAG_LID_CORNERS_MOVING
+        assert abs(cav.tau - p.tau) < 1e-15
+        cav.step(steps)
+        f, _, _, _ = gpu_state(cav)
+    fr, _, _, _ = oracle_state(p, steps)
+    assert (np.abs(f - fr) / np.abs(fr)).max() < 1e-12
+
+
 # ---------------------------------------------------------------- FP64 parity
 @pytest.mark.parametrize("nx,ny,steps,corners", [
     (128, 128, 1000, False),   # square cavity, Re = 100 (tau = 0.884)
