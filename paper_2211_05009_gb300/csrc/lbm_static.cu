@@ -129,6 +129,9 @@ extern "C" int lbm_stream_function_static(const double* ux, int nx, int ny, doub
     const long long ncb = (nx + kCols - 1) / kCols;
     const long long need = nseg * nx + 2 * nseg * ncb;
     if (need > LBM_STATIC_SCRATCH_DOUBLES) return LBM_ETOOBIG;  // grid too large for the fixed scratch
+    if (nseg > 65535) return LBM_ETOOBIG;                        // one grid row per segment (gridDim.y)
+    // An error pending from someone else's earlier call: report it, launch nothing, leave it set.
+    if (cudaPeekAtLastError() != cudaSuccess) return LBM_ECUDA;
     double* scratch = nullptr;
     if (scratch_for_current_device(&scratch) != cudaSuccess) {
         cudaGetLastError();
@@ -138,8 +141,11 @@ extern "C" int lbm_stream_function_static(const double* ux, int nx, int ny, doub
     double* part = scratch + nseg * nx;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const dim3 grid((unsigned)ncb, (unsigned)nseg);
+    // from here on a launch error is this call's own: take it (and clear it) after each launch
     k_static_seg<<<grid, kCols, 0, st>>>(ux, nx, ny, segsum);
+    if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
     k_static_walk<<<grid, kCols, 0, st>>>(ux, nx, ny, segsum, psi, part);
+    if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
     k_static_finalize<<<1, 32, 0, st>>>(part, (int)(nseg * ncb), nx, result);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }

@@ -9,6 +9,8 @@ other test first; it must also pass on its own in a fresh process.
 import numpy as np
 import pytest
 
+import oracle as O
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -34,7 +36,8 @@ def static_call(ux, ny, nx):
 
 def test_static_matches_context_entry_point_twice():
     """Two calls in a row (on two different fields and grid shapes): each must reproduce the
-    context-based result -- Psi to 1e-12 and the same minimum node."""
+    context-based result -- Psi to 1e-12 and the same minimum node -- and the CPU oracle's
+    stream function of the same u_x field (trapezoid rule from Psi = 0 on the bottom wall)."""
     for (nx, ny, steps) in [(200, 160, 700), (97, 133, 400)]:
         with Cavity(nx, ny, Re=400.0, U=0.1, dtype="f64") as cav:
             cav.step(steps)
@@ -43,6 +46,11 @@ def test_static_matches_context_entry_point_twice():
         assert torch.abs(psi - psi_ref).max().item() < 1e-12
         assert abs(res[0] - vmin) < 1e-12
         assert res[1] == xc and res[2] == yc
+        ux_h = ux.cpu().numpy()
+        psi_o, (omin, oi, oj), _ = O.stream_function(O.Params(nx, ny, 0.8, 0.1), ux_h)
+        assert np.abs(psi.cpu().numpy() - psi_o).max() < 1e-12
+        assert abs(res[0] - omin) < 1e-12
+        assert res[1] == oi / nx and res[2] == oj / nx
 
 
 def test_static_repeated_same_input_is_identical():
@@ -60,5 +68,9 @@ def test_static_rejects_grids_beyond_its_scratch():
     assert nx * ((ny + 31) // 32) > B.LBM_STATIC_SCRATCH_DOUBLES
     ux = torch.zeros(16, dtype=torch.float64, device="cuda")  # never read: rejected up front
     res = torch.zeros(3, dtype=torch.float64, device="cuda")
+    assert B.lbm_stream_function_static(ux, nx, ny, None, res) == B.LBM_ETOOBIG
+    # fits the scratch, but one launch row per 32-row segment exceeds the grid's y limit
+    nx, ny = 1, 3_000_000
+    assert nx * ((ny + 31) // 32) + 2 * ((ny + 31) // 32) <= B.LBM_STATIC_SCRATCH_DOUBLES
     assert B.lbm_stream_function_static(ux, nx, ny, None, res) == B.LBM_ETOOBIG
     assert B.lbm_stream_function_static(None, 16, 16, None, res) == B.LBM_EINVAL
