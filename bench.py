@@ -16,7 +16,8 @@ The metric is lattice updates per second (GLUPS = nx*ny*100 per step / time).
             steps, reads the residual and downloads rho, u_x, u_y with lbm_moments
   roofline  the step kernel: 18 populations x 4 bytes per node and launch / its average duration
   cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload (first steps of
-            the same 2048^2 cavity, one thread)
+            the same 2048^2 cavity): its OpenMP build on every host core, and the plain build
+            on one thread
 
 --impl reference runs that oracle as the reference arm.  Under torchrun (N > 1) every rank runs
 an independent replica (weak scaling; the path needs no exchange between cavities).
@@ -113,13 +114,14 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU oracle leg
-def oracle_sample(steps: int):
-    """FP64 oracle (single thread) on the first `steps` time steps of the benchmark cavity."""
+def oracle_sample(steps: int, openmp: bool = False):
+    """FP64 oracle on the first `steps` time steps of the benchmark cavity: the plain build on one
+    thread, or (openmp) the same source built with OpenMP on every host core."""
     import oracle as O
     p = O.Params.from_re(NX, NY, RE, U)
     f = O.init(p)
     t0 = time.perf_counter()
-    O.run(p, f, steps)
+    O.run(p, f, steps, openmp=openmp)
     dt = time.perf_counter() - t0
     return NX * NY * steps / dt / 1e9, dt
 
@@ -128,24 +130,26 @@ def reference_arm(args, rank):
     if rank != 0:
         return
     import oracle as O
-    O.build()
+    O.build(openmp=True)
+    cores = O.threads(openmp=True)
     p = O.Params.from_re(NX, NY, RE, U)
     f = O.init(p)
     for _ in range(args.warmup):
-        f = O.step(p, f)
+        f = O.step(p, f, openmp=True)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        f = O.step(p, f)
+        f = O.step(p, f, openmp=True)
     dt = time.perf_counter() - t0
     v = NX * NY * args.steps / dt / 1e9
-    sample = f"{args.steps} time steps of the 2048x2048 cavity (one oracle step per benchmark step)"
+    sample = (f"{args.steps} time steps of the 2048x2048 cavity (one oracle step per benchmark step), "
+              f"OpenMP build of the oracle on {cores} host threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "GLUPS", "n_gpus": 0,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "Re": RE, "U": U,
-                                        "oracle": "FP64 CPU, AoS, one thread"},
-        "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+                                        "oracle": f"FP64 CPU, AoS, {cores} threads"},
+        "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -298,10 +302,17 @@ def our_arm(args, rank, world, local_rank):
     if not args.no_cpu_baseline and world == 1:
         import oracle as O
         O.build()
-        steps_cpu = 64  # about 14 s of single-thread oracle work
-        v, dt = oracle_sample(steps_cpu)
-        cpu = {"value": v, "unit": "GLUPS", "cores": 1, "kind": "oracle",
-               "sample": f"first {steps_cpu} time steps of the same 2048x2048 cavity ({dt:.1f} s, FP64, one thread)"}
+        O.build(openmp=True)
+        cores = O.threads(openmp=True)
+        steps_1 = 64  # about 14 s of single-thread oracle work
+        v1, dt1 = oracle_sample(steps_1)
+        steps_n = 64 * max(1, min(16, cores // 2))  # about the same wall time on all cores
+        vn, dtn = oracle_sample(steps_n, openmp=True)
+        cpu = {"value": vn, "unit": "GLUPS", "cores": cores, "kind": "oracle",
+               "sample": f"first {steps_n} time steps of the same 2048x2048 cavity ({dtn:.1f} s, FP64, "
+                         f"OpenMP build on {cores} host threads)",
+               "single_thread": {"value": v1, "unit": "GLUPS", "cores": 1,
+                                 "sample": f"first {steps_1} time steps ({dt1:.1f} s, plain build, one thread)"}}
     line = {
         "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,

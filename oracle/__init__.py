@@ -28,6 +28,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liblbm_oracle.so")
+_OMP_PATH = os.path.join(_HERE, "liblbm_oracle_omp.so")  # the same source with -fopenmp
 
 CAVITY_NEE, CAVITY_BB, PERIODIC, CHANNEL_NEE = 0, 1, 2, 3
 
@@ -45,43 +46,64 @@ class _Params(ctypes.Structure):
     ]
 
 
-def build(force: bool = False) -> str:
-    """Compile lbm_oracle.c into liblbm_oracle.so next to it (gcc, -O2, no FMA contraction)."""
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile lbm_oracle.c into liblbm_oracle.so next to it (gcc, -O2, no FMA contraction).
+
+    openmp=True builds the same source with -fopenmp into liblbm_oracle_omp.so: the node loops of
+    a time step run on all host cores, with bitwise the same result (every node's arithmetic is
+    unchanged).  It exists to time the oracle on all cores; the tests check it equals the plain
+    build."""
+    path = _OMP_PATH if openmp else _LIB_PATH
+    if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+        tmp = path + f".tmp{os.getpid()}"
         subprocess.check_call(
             ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-             "-std=c11", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+             "-std=c11", *(["-fopenmp"] if openmp else []), "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, path)
+    return path
 
 
 _lib = None
+_lib_omp = None
 
 
-def _L():
-    global _lib
+def _L(openmp: bool = False):
+    global _lib, _lib_omp
+    if openmp:
+        if _lib_omp is None:
+            _lib_omp = _bind(ctypes.CDLL(build(openmp=True)))
+        return _lib_omp
     if _lib is None:
-        lib = ctypes.CDLL(build())
-        dp = ctypes.POINTER(ctypes.c_double)
-        pp = ctypes.POINTER(_Params)
-        ip = ctypes.POINTER(ctypes.c_int)
-        lib.orc_feq.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
-        lib.orc_step.argtypes = [pp, dp, dp]
-        lib.orc_step_node.argtypes = [pp, dp, ctypes.c_int, ctypes.c_int, dp]
-        lib.orc_init.argtypes = [pp, dp]
-        lib.orc_init_moments.argtypes = [pp, dp, dp, dp, dp]
-        lib.orc_init_moments_neq.argtypes = [pp, dp, dp, dp, dp]
-        lib.orc_moments.argtypes = [pp, dp, dp, dp, dp]
-        lib.orc_residual.argtypes = [ctypes.c_size_t, dp, dp, dp, dp]
-        lib.orc_residual.restype = ctypes.c_double
-        lib.orc_mass.argtypes = [pp, dp]
-        lib.orc_mass.restype = ctypes.c_double
-        lib.orc_stream_function.argtypes = [pp, dp, dp, dp, ip, ip, dp, ip, ip]
-        lib.orc_run.argtypes = [pp, dp, dp, ctypes.c_long]
-        lib.orc_run.restype = ctypes.c_int
-        _lib = lib
+        _lib = _bind(ctypes.CDLL(build()))
     return _lib
+
+
+def _bind(lib):
+    dp = ctypes.POINTER(ctypes.c_double)
+    pp = ctypes.POINTER(_Params)
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.orc_feq.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+    lib.orc_step.argtypes = [pp, dp, dp]
+    lib.orc_step_node.argtypes = [pp, dp, ctypes.c_int, ctypes.c_int, dp]
+    lib.orc_init.argtypes = [pp, dp]
+    lib.orc_init_moments.argtypes = [pp, dp, dp, dp, dp]
+    lib.orc_init_moments_neq.argtypes = [pp, dp, dp, dp, dp]
+    lib.orc_moments.argtypes = [pp, dp, dp, dp, dp]
+    lib.orc_residual.argtypes = [ctypes.c_size_t, dp, dp, dp, dp]
+    lib.orc_residual.restype = ctypes.c_double
+    lib.orc_mass.argtypes = [pp, dp]
+    lib.orc_mass.restype = ctypes.c_double
+    lib.orc_stream_function.argtypes = [pp, dp, dp, dp, ip, ip, dp, ip, ip]
+    lib.orc_run.argtypes = [pp, dp, dp, ctypes.c_long]
+    lib.orc_run.restype = ctypes.c_int
+    lib.orc_threads.argtypes = []
+    lib.orc_threads.restype = ctypes.c_int
+    return lib
+
+
+def threads(openmp: bool = False) -> int:
+    """Host threads the time step of the plain (1) or the OpenMP build uses."""
+    return _L(openmp).orc_threads()
 
 
 def _dp(a: np.ndarray):
@@ -142,11 +164,11 @@ def init_moments_neq(p: Params, rho, ux, uy) -> np.ndarray:
     return f
 
 
-def step(p: Params, f: np.ndarray) -> np.ndarray:
-    """One time step; returns the new post-collision field."""
+def step(p: Params, f: np.ndarray, openmp: bool = False) -> np.ndarray:
+    """One time step; returns the new post-collision field (openmp: the all-core build)."""
     f = np.ascontiguousarray(f, dtype=np.float64)
     out = np.empty_like(f)
-    _L().orc_step(ctypes.byref(p.c()), _dp(f), _dp(out))
+    _L(openmp).orc_step(ctypes.byref(p.c()), _dp(f), _dp(out))
     return out
 
 
@@ -157,11 +179,12 @@ def step_node(p: Params, f: np.ndarray, x: int, y: int) -> np.ndarray:
     return out
 
 
-def run(p: Params, f: np.ndarray, n: int) -> np.ndarray:
-    """n time steps from f; returns the new field (f is not modified)."""
+def run(p: Params, f: np.ndarray, n: int, openmp: bool = False) -> np.ndarray:
+    """n time steps from f; returns the new field (f is not modified).  openmp=True runs the
+    OpenMP build of the same source (all host cores, bitwise the same result)."""
     f = np.array(f, dtype=np.float64, order="C", copy=True)
     tmp = np.empty_like(f)
-    rc = _L().orc_run(ctypes.byref(p.c()), _dp(f), _dp(tmp), int(n))
+    rc = _L(openmp).orc_run(ctypes.byref(p.c()), _dp(f), _dp(tmp), int(n))
     if rc:
         raise FloatingPointError("oracle: non-finite population")
     return f

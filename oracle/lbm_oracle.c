@@ -24,6 +24,12 @@
  *  - the NEE reference node x_f is the inner neighbour along the inward normal
  *    (the diagonal inner node for corners), and the wall density is rho_f
  *
+ * Threads: compiled a second time with -fopenmp (liblbm_oracle_omp.so), the three node loops
+ * of orc_step split their rows over the host's cores.  Every node is still computed by the
+ * same arithmetic from the same inputs (step 2 reads only fluid nodes written in step 1), so
+ * the result is bitwise that of the single-thread build; without -fopenmp the pragmas are
+ * ignored.
+ *
  * Test-only boundary modes (not in the paper; they exist to pin the oracle against
  * closed forms): halfway bounce-back cavity, fully periodic box, and a channel that is
  * periodic in x with NEE walls on rows 0 and ny-1; an optional body force uses the
@@ -31,6 +37,9 @@
  */
 #include <math.h>
 #include <stddef.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -169,17 +178,20 @@ void orc_step(const orc_params *p, const double *fin, double *fout)
     double uwx, uwy;
     int xf, yf;
     /* 1. streaming into fout (fluid nodes only) */
+#pragma omp parallel for private(uwx, uwy, xf, yf) schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             if (nee_wall(p, x, y, &uwx, &uwy, &xf, &yf)) continue;
             pull_node(p, fin, x, y, &fout[node(p, x, y) * 9]);
         }
     /* 2. non-equilibrium extrapolation at wall nodes, from the streamed reference nodes */
+#pragma omp parallel for private(uwx, uwy, xf, yf) schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x)
             if (nee_wall(p, x, y, &uwx, &uwy, &xf, &yf))
                 nee_set(&fout[node(p, xf, yf) * 9], uwx, uwy, &fout[node(p, x, y) * 9]);
     /* 3. collision at every node (no body force on wall nodes) */
+#pragma omp parallel for private(uwx, uwy, xf, yf) schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             double tmp[9];
@@ -331,6 +343,16 @@ void orc_stream_function(const orc_params *p, const double *ux, double *psi, dou
             if (v < *psi_min) { *psi_min = v; *imin = x; *jmin = y; }
             if (v > *psi_max) { *psi_max = v; *imax = x; *jmax = y; }
         }
+}
+
+/* Host threads the node loops of orc_step use: 1 unless built with -fopenmp. */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* Convenience driver: n steps from f (in place), ping-ponging through tmp.

@@ -314,3 +314,15 @@ def test_neq_start_removes_the_initial_layer():
     decay from the first step.  A wrong sign or scale of the added part fails this."""
     e_eq, e_neq = _tg_start_error(False), _tg_start_error(True)
     assert e_neq < e_eq / 5, (e_eq, e_neq)
+
+
+def test_openmp_build_is_bitwise_the_plain_build():
+    """The all-core build of the same C source (used to time the oracle on every host core)
+    computes every node as the plain build does: fields bitwise equal after 40 steps of a ragged
+    cavity with moving lid corners, started from perturbed populations."""
+    p = O.Params(67, 41, 0.56, 0.1, corner_moving=True)
+    f0 = _random_field(p, 1)
+    a = O.run(p, f0, 40)
+    b = O.run(p, f0, 40, openmp=True)
+    assert np.array_equal(a, b)
+    assert O.threads() == 1 and O.threads(openmp=True) >= 1
