@@ -243,6 +243,18 @@ int lbm_probe_clear(lbm_ctx *ctx);
 int lbm_stream_function_static(const double *ux, int nx, int ny, double *psi, double *result,
                                void *stream);
 
+/* ------------------------------------------------------------------ ALU throughput */
+
+/* Fused multiply-add throughput of the current device, in FLOP/s (2 per FMA), FP64 (fp64 != 0)
+ * or FP32 -- the ALU denominator of the step kernels' roofline where memory bandwidth is not the
+ * bound (no counterpart in the paper; GB300's FP64 rate is a small fraction of its FP32 rate).
+ * A kernel of 8 blocks x 256 threads per SM runs 8 independent FMA chains per thread for
+ * trips x 16 chain steps (1 <= trips <= 1e6); 3 warm-up launches, then the best of 5 timed with
+ * CUDA events on the legacy stream.  *flops_per_s and *ms (host, may be NULL) receive the rate
+ * and that launch's time.  Allocates and frees a small output array.  Synchronising.
+ * Errors: LBM_EINVAL (trips), LBM_ENOMEM, LBM_ECUDA. */
+int lbm_fma_peak(int fp64, int trips, double *flops_per_s, double *ms);
+
 /* ------------------------------------------------------------------ batched sweep */
 
 /* A set of independent cavities of uneven sizes stepped together in one persistent GPU launch per

@@ -117,6 +117,7 @@ _SIGS = [
     ("lbm_warm_smooth", _I, [_P, _I, _I, _I, _I, _P, _P]),
     ("lbm_nn_gemm_bf16", _I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _I, _P]),
     ("lbm_nn_gemm_bf16_tc05", _I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _I, _I, _P, _P]),
+    ("lbm_fma_peak", _I, [_I, _I, _DP, _DP]),
     ("lbm_save", _I, [_P, ctypes.c_char_p]),
     ("lbm_load", _I, [_P, ctypes.c_char_p]),
 ]
@@ -534,3 +535,10 @@ def lbm_nn_gemm_bf16(M, N, K, A, lda, B, ldb, C, ldc, op=0, split_k=1, stream_ha
 def lbm_nn_gemm_bf16_tc05(M, N, K, A, lda, B, ldb, C, ldc, op, err, trans_c=0, split_k=1, stream_handle=None) -> int:
     return library().lbm_nn_gemm_bf16_tc05(M, N, K, _tptr(A), lda, _tptr(B), ldb, _tptr(C), ldc, op, trans_c, split_k,
                                            _tptr(err), stream_handle)
+
+
+def lbm_fma_peak(fp64: bool = True, trips: int = 2000):
+    """(FLOP/s, milliseconds of the timed launch) of the device's FMA pipe, FP64 or FP32."""
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    _check(None, library().lbm_fma_peak(1 if fp64 else 0, trips, ctypes.byref(rate), ctypes.byref(ms)))
+    return rate.value, ms.value
