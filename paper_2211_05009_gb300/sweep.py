@@ -28,15 +28,30 @@ RE_DEFAULT = "4000,5000,6000,7000,8000"
 AR_DEFAULT = "0.4,0.6,0.8,1.0,1.2,1.4,1.6,1.8,2.0"
 
 
-def cavity_list(nx, res, ars, U):
-    cases = []
-    for ar in ars:
-        for re in res:
-            cases.append({"Re": re, "Ar": ar, "nx": nx, "ny": int(round(nx * ar)), "U": U})
+# (Ar, Re) pairs at which Sec. 3.3 reports a flow state: the periodic entries of Table 3, and the
+# cavities of Figs. 8-10 (Re 6000, 6500 and 8000 at Ar 0.5, 0.6, 0.8, 1.1, 1.2, 1.5, 1.6).
+TABLE3_PAIRS = [(0.4, 8000)] + [(0.5, r) for r in (6500, 7000, 7500)] + \
+    [(0.6, r) for r in (5500, 6000, 6500, 7000, 7500, 8000)] + \
+    [(0.7, r) for r in (5000, 5500, 6000, 6500, 7000, 7500)] + [(0.8, 6000), (0.8, 6500)] + \
+    [(1.2, r) for r in (4500, 5000, 5500, 6000)] + [(1.3, r) for r in (4500, 5000, 5500, 6000, 6500)] + \
+    [(1.4, r) for r in (5000, 5500, 6000, 6500, 7000)] + [(1.7, 6500), (1.7, 7000)] + \
+    [(1.8, 7000), (1.8, 7500), (1.9, 7000), (1.9, 7500)]
+FIG8_10_PAIRS = [(ar, re) for re in (6000, 6500, 8000) for ar in (0.5, 0.6, 0.8, 1.1, 1.2, 1.5, 1.6)]
+
+
+def cavity_list(nx, res, ars, U, extra_pairs=()):
+    """The Re x Ar grid, then any (Ar, Re) pairs not on it, as cavities of nx x round(nx Ar)."""
+    cases, seen = [], set()
+    for ar, re in [(ar, re) for ar in ars for re in res] + list(extra_pairs):
+        key = (round(float(ar), 6), round(float(re), 6))
+        if key in seen:
+            continue
+        seen.add(key)
+        cases.append({"Re": float(re), "Ar": float(ar), "nx": nx, "ny": int(round(nx * ar)), "U": U})
     return cases
 
 
-def run_batched(cases, dtype, tol, max_steps, every, cap, tune_steps=50):
+def run_batched(cases, dtype, tol, max_steps, every, cap, tune_steps=50, save_series=None):
     st = torch.cuda.current_stream()
     b = B.lbm_batch_create([c["nx"] for c in cases], [c["ny"] for c in cases], [c["Re"] for c in cases],
                            [c["U"] for c in cases], dtype)
@@ -58,6 +73,9 @@ def run_batched(cases, dtype, tol, max_steps, every, cap, tune_steps=50):
         shape, rows, blocks, graphs = B.lbm_batch_launch_info(b)
         out = []
         ser = series.cpu().numpy()
+        if save_series:  # raw probe ring buffers [cavity][sample mod cap][u_x, u_y] and steps taken
+            np.savez_compressed(save_series, series=ser.astype(np.float32), steps=np.asarray(done), every=every,
+                                re=np.array([c["Re"] for c in cases]), ar=np.array([c["Ar"] for c in cases]))
         for i, c in enumerate(cases):
             n = int(done[i]) // every
             k = min(n, cap)
@@ -115,15 +133,19 @@ def main(argv=None):
     ap.add_argument("--probe-every", type=int, default=100)
     ap.add_argument("--sequential", action="store_true", help="also run the one-at-a-time arm")
     ap.add_argument("--autotune-steps", type=int, default=50, help="steps per tile-shape trial (0: keep the default shape)")
+    ap.add_argument("--save-series", default=None, help="write the probe series of the batched arm (.npz)")
+    ap.add_argument("--paper-pairs", action="store_true",
+                    help="add every (Ar, Re) at which Sec. 3.3 reports a state (Table 3, Figs. 8-10)")
     a = ap.parse_args(argv)
     build()
     res = [float(v) for v in a.re.split(",")]
     ars = [float(v) for v in a.ar.split(",")]
-    cases = cavity_list(a.nx, res, ars, a.u)
+    cases = cavity_list(a.nx, res, ars, a.u, TABLE3_PAIRS + FIG8_10_PAIRS if a.paper_pairs else ())
     cap = max(8, a.max_steps // a.probe_every)
     doc = {"nx": a.nx, "U": a.u, "dtype": a.dtype, "tol": a.tol, "max_steps": a.max_steps,
            "n_cavities": len(cases), "nodes": sum(c["nx"] * c["ny"] for c in cases)}
-    doc["batched"] = run_batched(cases, a.dtype, a.tol, a.max_steps, a.probe_every, cap, a.autotune_steps)
+    doc["batched"] = run_batched(cases, a.dtype, a.tol, a.max_steps, a.probe_every, cap, a.autotune_steps,
+                                 a.save_series)
     if a.sequential:
         doc["sequential"] = run_sequential(cases, a.dtype, a.tol, a.max_steps)
         doc["speedup_time_to_steady"] = doc["sequential"]["wall_s"] / doc["batched"]["wall_s"]
