@@ -43,3 +43,20 @@ def test_observing_points_of_sec_3_3():
     assert observing_point(0.4) == (0.5, 0.2)
     assert observing_point(0.5) == observing_point(0.6) == (0.5, 0.3)
     assert observing_point(1.2) == (0.5, 0.5)
+
+
+def test_sweep_pairs_cover_every_state_the_paper_reports():
+    """The sweep's paper pairs are exactly the periodic entries of Table 3 plus the Fig. 8-10
+    cavities (golden files, transcribed from the paper), and its case list has no duplicates."""
+    import os
+    from paper_2211_05009_gb300 import sweep as S
+    gold = os.path.join(os.path.dirname(__file__), "golden")
+    t3 = {(float(a), float(r)) for a, r, _ in
+          (ln.split() for ln in open(os.path.join(gold, "table3_periods.txt")) if ln[0].isdigit())}
+    assert t3 == {(float(a), float(r)) for a, r in S.TABLE3_PAIRS} and len(t3) == 38
+    st = {(float(a), float(r)) for r, a, *_ in
+          (ln.split() for ln in open(os.path.join(gold, "states_sec33.txt")) if ln[0].isdigit())}
+    assert st == {(float(a), float(r)) for a, r in S.FIG8_10_PAIRS} and len(st) == 21
+    cases = S.cavity_list(500, [4000.0, 8000.0], [0.6, 1.2], 0.1, S.TABLE3_PAIRS + S.FIG8_10_PAIRS)
+    keys = [(c["Ar"], c["Re"]) for c in cases]
+    assert len(keys) == len(set(keys)) and all(c["ny"] == round(500 * c["Ar"]) for c in cases)
