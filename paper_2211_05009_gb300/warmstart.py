@@ -105,7 +105,7 @@ def target_tensor(fields, nx, ny, H):
     return t
 
 
-def main(argv=None):
+def parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=256)
     ap.add_argument("--test", type=int, default=64)
@@ -127,7 +127,12 @@ def main(argv=None):
     ap.add_argument("--coarse-re-max", type=float, default=1e9)
     ap.add_argument("--smooth", type=int, default=4, help="box-filter passes over the network's correction")
     ap.add_argument("--out", default=None)
-    a = ap.parse_args(argv)
+    return ap
+
+
+def run(a) -> dict:
+    """The whole pipeline (coarse runs, targets, training, gate, evaluation) for parsed arguments
+    `a`; returns the report."""
     build()
     torch.manual_seed(0)
     st = torch.cuda.current_stream()
@@ -285,7 +290,11 @@ def main(argv=None):
     report["arms"] = arms
     report["draws_test"] = test
     B.lbm_net_destroy(net)
-    print(json.dumps(report), flush=True)
+    return report
+
+
+def main(argv=None):
+    print(json.dumps(run(parser().parse_args(argv))), flush=True)
 
 
 if __name__ == "__main__":

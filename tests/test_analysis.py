@@ -24,6 +24,34 @@ def test_sinusoid_is_periodic_with_its_period():
     assert abs(s.period_convective - period * 0.1 / 500) < 0.02 * period * 0.1 / 500
 
 
+def test_drifting_periodic_signal_is_periodic():
+    """A cycle on a slow linear drift (the wall mass leak of long runs) is still periodic."""
+    every, period = 100, 5011.0
+    t = np.arange(6000) * every
+    ux = 0.02 + 2e-3 * np.sin(2 * np.pi * t / period) + 4e-8 * t
+    s = classify(ux, every=every, U=0.1, nx=500)
+    assert s.state == "periodic" and abs(s.period_steps - period) < 0.02 * period
+
+
+def test_oscillation_below_plot_resolution_is_steady():
+    """Peak-to-peak 4e-5 U: below the 1e-3 U an oscillation needs to show in a U_x plot."""
+    t = np.arange(4000) * 100
+    ux = 0.03 + 2e-6 * np.sin(2 * np.pi * t / 7000.0)
+    s = classify(ux, every=100, U=0.1, nx=500)
+    assert s.state == "steady" and s.amplitude < 1e-3 * 0.1
+
+
+def test_modulated_cycle_is_aperiodic_with_its_dominant_period():
+    """Amplitude modulation by an incommensurate slow cycle: not periodic, but the carrier period
+    is reported as the dominant one."""
+    every, period = 100, 3000.0
+    t = np.arange(8000) * every
+    ux = 0.02 + 2e-3 * np.sin(2 * np.pi * t / period) * (1 + 0.3 * np.sin(2 * np.pi * t / (period * 7.31)))
+    s = classify(ux, every=every, U=0.1, nx=500)
+    assert s.state == "aperiodic"
+    assert s.dominant_period_steps is not None and abs(s.dominant_period_steps - period) < 0.03 * period
+
+
 def test_incommensurate_and_noisy_signal_is_aperiodic():
     rng = np.random.default_rng(0)
     t = np.arange(4000, dtype=float)
