@@ -67,7 +67,8 @@ def test_python_package_does_no_method_arithmetic():
     for path in glob.glob(os.path.join(pkg, "*.py")):
         code = "\n".join(l.split("#")[0] for l in open(path).read().splitlines())
         assert not re.search(r"\b(tau|nu)\s*=[^=].*\b(Re|re)\b", code), path
-        assert not re.search(r"\+\s*0\.5\b", code), path
+        assert not re.search(r"\b3(\.0)?\s*\*[^\n]*\+\s*0\.5\b", code), path  # tau = 3 nu + 1/2
+        assert not re.search(r"\(\s*tau\s*-\s*0\.5\s*\)", code), path  # nu = (tau - 1/2)/3
 
 
 def test_create_without_gpu_fails_loudly(lib):
