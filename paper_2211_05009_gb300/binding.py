@@ -20,7 +20,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EDIVERGED, LBM_ETIMEOUT, LBM_ENOT
 ERROR_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_EDIVERGED",
                5: "LBM_ETIMEOUT", 6: "LBM_ENOTREADY", 7: "LBM_EIO", 8: "LBM_ETOOBIG"}
 LBM_STATIC_SCRATCH_DOUBLES = 1 << 19
-DTYPES = {"f64": 0, "f32": 1, "f32s": 2, "f16s": 3, "bf16s": 4}
+DTYPES = {"f64": 0, "f32": 1, "f32s": 2, "f16s": 3, "bf16s": 4, "q16s": 5}
 LBM_FLAG_LID_CORNERS_MOVING = 1
 LBM_MAX_PROBES = 4
 LBM_BATCH_SHAPES = 8

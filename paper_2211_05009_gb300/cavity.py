@@ -15,7 +15,7 @@ class Cavity:
     """A D2Q9 lid-driven cavity of nx x ny nodes (walls included) on cuda:0.
 
     Either ``Re`` (tau from Re = U nx / nu, nu = (tau - 1/2)/3) or ``tau`` must be given.
-    ``dtype`` is the population storage: f64, f32, f32s, f16s or bf16s.
+    ``dtype`` is the population storage: f64, f32, f32s, f16s, bf16s or q16s.
     """
 
     def __init__(self, nx: int, ny: int, Re: float | None = None, U: float = 0.1, dtype: str = "f32s",

@@ -64,6 +64,7 @@ struct lbm_ctx {
 
     ProbeSet probes{};
     int cfg = 0;  // launch shape of the step kernel
+    QCodec q{};   // LBM_Q16S scales (from U at creation)
     StepGeometry geo{};
     std::string err;
 
@@ -105,6 +106,8 @@ struct lbm_ctx {
         a.plane = plane;
         a.U = U;
         a.corner_moving = (flags & LBM_FLAG_LID_CORNERS_MOVING) ? 1 : 0;
+        a.q = q;
+        a.st = d_state;
         return a;
     }
     FieldArgs cur() const { return field((int)(step & 1)); }
@@ -127,6 +130,7 @@ struct lbm_ctx {
         a.probes = probes;
         a.snap = snap;
         a.partials = partials;
+        a.q = q;
         return a;
     }
 
@@ -269,7 +273,7 @@ extern "C" int lbm_create_ex(int nx, int ny, double tau, double U, lbm_dtype dty
     if (nx < 3 || ny < 3) return create_fail(nullptr, LBM_EINVAL, fmt("grid %d x %d: need nx, ny >= 3", nx, ny));
     if (!(tau > 0.5) || !std::isfinite(tau)) return create_fail(nullptr, LBM_EINVAL, fmt("tau = %g: need tau > 1/2", tau));
     if (!std::isfinite(U)) return create_fail(nullptr, LBM_EINVAL, "U is not finite");
-    if ((int)dtype < 0 || (int)dtype > 4) return create_fail(nullptr, LBM_EINVAL, fmt("unknown dtype %d", (int)dtype));
+    if ((int)dtype < 0 || (int)dtype > 5) return create_fail(nullptr, LBM_EINVAL, fmt("unknown dtype %d", (int)dtype));
     if (flags & ~LBM_FLAG_LID_CORNERS_MOVING) return create_fail(nullptr, LBM_EINVAL, "unknown flags");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -288,6 +292,7 @@ extern "C" int lbm_create_ex(int nx, int ny, double tau, double U, lbm_dtype dty
     c->release = g_release;
     c->alloc_user = g_alloc_user;
     c->pitch = row_pitch(c->dtype, nx);
+    c->q = q16_codec(U);
     c->plane = c->pitch * (long long)ny;
     c->cfg = default_step_config(c->dtype);
     c->geo = step_geometry(c->dtype, c->cfg, ny, c->pitch);
@@ -318,12 +323,13 @@ extern "C" int lbm_create_ex(int nx, int ny, double tau, double U, lbm_dtype dty
     for (auto& e : c->ev)
         if ((rc = c->cuda(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event create")))
             return create_fail(c, rc, "");
+    // the device state first: the LBM_Q16S initial state is stored against its reference density
+    if ((rc = c->cuda(cudaMemsetAsync(c->d_state, 0, sizeof(DevState), c->stream), "state reset")))
+        return create_fail(c, rc, "");
     // both buffers hold the initial state, so padding is defined in either
     for (int b = 0; b < 2; ++b)
         if ((rc = c->cuda(launch_init(c->dtype, c->field(b), c->snap, c->stream), "init kernel launch")))
             return create_fail(c, rc, "");
-    if ((rc = c->cuda(cudaMemsetAsync(c->d_state, 0, sizeof(DevState), c->stream), "state reset")))
-        return create_fail(c, rc, "");
     if ((rc = c->sync())) return create_fail(c, rc, "");
     *out = c;
     return LBM_OK;
@@ -607,9 +613,11 @@ extern "C" int lbm_set_moments_ex(lbm_ctx* c, const double* rho, const double* u
     c->step = 0;
     for (int q = 0; q < c->probes.n; ++q) c->probes.start[q] = 0;
     c->invalidate_graphs();
-    rc = c->cuda(launch_set_moments(c->dtype, c->cur(), dv[0], dv[1], dv[2], c->snap,
-                                    (flags & LBM_INIT_NEQ) ? c->tau : 0.0, c->stream), "set_moments launch");
-    if (!rc) rc = c->cuda(cudaMemsetAsync(c->d_state, 0, sizeof(DevState), c->stream), "state reset");
+    // the state reset comes first: the LBM_Q16S populations are stored against its reference density
+    rc = c->cuda(cudaMemsetAsync(c->d_state, 0, sizeof(DevState), c->stream), "state reset");
+    if (!rc)
+        rc = c->cuda(launch_set_moments(c->dtype, c->cur(), dv[0], dv[1], dv[2], c->snap,
+                                        (flags & LBM_INIT_NEQ) ? c->tau : 0.0, c->stream), "set_moments launch");
     if (!rc && off) rc = c->sync();  // the staged host input may be reused after return
     return rc;
 }
@@ -771,7 +779,7 @@ extern "C" int lbm_save(lbm_ctx* c, const char* path) {
     }
     FileHeader h{};
     memcpy(h.magic, kMagic, 8);
-    h.version = 1;
+    h.version = 2;
     h.nx = c->nx;
     h.ny = c->ny;
     h.dtype = c->dtype;
@@ -792,7 +800,7 @@ extern "C" int lbm_load(lbm_ctx* c, const char* path) {
     FILE* fp = fopen(path, "rb");
     if (!fp) return c->fail(LBM_EIO, fmt("cannot open %s", path));
     FileHeader h{};
-    if (fread(&h, sizeof h, 1, fp) != 1 || memcmp(h.magic, kMagic, 8) != 0 || h.version != 1) {
+    if (fread(&h, sizeof h, 1, fp) != 1 || memcmp(h.magic, kMagic, 8) != 0 || h.version != 2) {
         fclose(fp);
         return c->fail(LBM_EIO, "not a checkpoint of this library");
     }

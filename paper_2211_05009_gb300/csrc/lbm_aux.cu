@@ -30,22 +30,48 @@ __device__ __forceinline__ C geq_c(int j, C drho, C ux, C uy) {
     return C(wd(j)) * (drho + (C(1.0) + drho) * A);
 }
 
+// LBM_Q16S reference density of the stored populations (0 for the other storage types).
+template <typename S>
+__device__ __forceinline__ float ref_density(const FieldArgs& a) {
+    if constexpr (kIsQ16<S>) return float(__ldcg(&a.st->rho_ref[0]));
+    else return 0.f;
+}
+
+// g_j = f_j - w_j of one stored population (sref: ref_density).
 template <typename S, bool SHIFTED>
-__device__ __forceinline__ typename St<S>::C load_g(const S* f, long long idx, int j) {
+__device__ __forceinline__ typename St<S>::C load_g(const S* f, long long idx, int j, const QCodec& q,
+                                                    float sref) {
     using C = typename St<S>::C;
-    const C v = St<S>::to(f[idx]);
-    return SHIFTED ? v : v - C(wd(j));
+    if constexpr (kIsQ16<S>) {
+        return fmaf(float(wd(j)), sref, q16_decode(f[idx].bits, q.dec[j]));
+    } else {
+        const C v = St<S>::to(f[idx]);
+        return SHIFTED ? v : v - C(wd(j));
+    }
+}
+
+// Store g_j = f_j - w_j as one population.
+template <typename S, bool SHIFTED>
+__device__ __forceinline__ void store_g(S* f, long long idx, int j, typename St<S>::C g, const QCodec& q,
+                                        float sref) {
+    using C = typename St<S>::C;
+    if constexpr (kIsQ16<S>) {
+        bool sat = false;
+        f[idx].bits = (unsigned short)q16_encode(g - float(wd(j)) * sref, q.enc[j], sat);
+    } else {
+        f[idx] = St<S>::from(SHIFTED ? g : g + C(wd(j)));
+    }
 }
 
 // Moments (Eq. 3) of the stored populations at linear index k.
 template <typename S, bool SHIFTED>
-__device__ __forceinline__ void node_moments(const S* f, long long plane, long long k,
-                                             typename St<S>::C& drho, typename St<S>::C& ux,
+__device__ __forceinline__ void node_moments(const S* f, long long plane, long long k, const QCodec& q,
+                                             float sref, typename St<S>::C& drho, typename St<S>::C& ux,
                                              typename St<S>::C& uy) {
     using C = typename St<S>::C;
     C g[9];
 #pragma unroll
-    for (int j = 0; j < 9; ++j) g[j] = load_g<S, SHIFTED>(f, j * plane + k, j);
+    for (int j = 0; j < 9; ++j) g[j] = load_g<S, SHIFTED>(f, j * plane + k, j, q, sref);
     drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
     const C rho = C(1.0) + drho;
     ux = ((g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7])) / rho;
@@ -95,6 +121,7 @@ __global__ void k_init(FieldArgs a, void* snap_v, const double* rho_in, const do
         }
     }
     const C tau = C(neq_tau), keep = neq ? C(1.0) - C(1.0) / tau : C(0);
+    const float sref = ref_density<S>(a);
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
         C g = geq_c<C>(j, drho, ux, uy);
@@ -104,7 +131,7 @@ __global__ void k_init(FieldArgs a, void* snap_v, const double* rho_in, const do
             const C qdu = qxx * dxux + qxy * (dxuy + dyux) + qyy * dyuy;
             g += keep * (-C(3.0) * tau * C(wd(j)) * (C(1.0) + drho) * qdu);
         }
-        f[j * a.plane + k] = St<S>::from(SHIFTED ? g : g + C(wd(j)));
+        store_g<S, SHIFTED>(f, j * a.plane + k, j, g, a.q, sref);
     }
     if (snap_v) {
         C* snap = static_cast<C*>(snap_v);
@@ -122,7 +149,7 @@ __global__ void k_moments(FieldArgs a, double* rho, double* ux, double* uy) {
     if (x >= a.nx) return;
     const S* f = static_cast<const S*>(a.f);
     C drho, u, v;
-    node_moments<S, SHIFTED>(f, a.plane, (long long)y * a.pitch + x, drho, u, v);
+    node_moments<S, SHIFTED>(f, a.plane, (long long)y * a.pitch + x, a.q, ref_density<S>(a), drho, u, v);
     const long long d = (long long)y * a.nx + x;
     if (rho) rho[d] = 1.0 + double(drho);
     if (ux) ux[d] = double(u);
@@ -135,8 +162,11 @@ __global__ void k_get_pop(FieldArgs a, double* out) {
     const int y = blockIdx.y, j = blockIdx.z;
     if (x >= a.nx) return;
     const S* f = static_cast<const S*>(a.f);
-    const double v = double(St<S>::to(f[j * a.plane + (long long)y * a.pitch + x]));
-    out[((long long)j * a.ny + y) * a.nx + x] = SHIFTED ? v + wd(j) : v;
+    const long long k = j * a.plane + (long long)y * a.pitch + x;
+    double v;
+    if constexpr (kIsQ16<S>) v = double(load_g<S, SHIFTED>(f, k, j, a.q, ref_density<S>(a))) + wd(j);
+    else v = SHIFTED ? double(St<S>::to(f[k])) + wd(j) : double(St<S>::to(f[k]));
+    out[((long long)j * a.ny + y) * a.nx + x] = v;
 }
 
 template <typename S, bool SHIFTED>
@@ -147,7 +177,9 @@ __global__ void k_set_pop(FieldArgs a, const double* in) {
     if (x >= a.nx) return;
     S* f = static_cast<S*>(a.f);
     const double v = in[((long long)j * a.ny + y) * a.nx + x];
-    f[j * a.plane + (long long)y * a.pitch + x] = St<S>::from(C(SHIFTED ? v - wd(j) : v));
+    const long long k = j * a.plane + (long long)y * a.pitch + x;
+    if constexpr (kIsQ16<S>) store_g<S, SHIFTED>(f, k, j, C(v - wd(j)), a.q, ref_density<S>(a));
+    else f[k] = St<S>::from(C(SHIFTED ? v - wd(j) : v));
 }
 
 // ------------------------------------------------------------------ mass
@@ -156,13 +188,14 @@ __global__ void __launch_bounds__(256) k_mass(FieldArgs a, double* partials) {
     using C = typename St<S>::C;
     __shared__ double sh[8];
     const S* f = static_cast<const S*>(a.f);
+    const float sref = ref_density<S>(a);
     double acc = 0.0;
     for (int y = blockIdx.x; y < a.ny; y += gridDim.x)
         for (int x = threadIdx.x; x < a.nx; x += blockDim.x) {
             const long long k = (long long)y * a.pitch + x;
             C g[9];
 #pragma unroll
-            for (int j = 0; j < 9; ++j) g[j] = load_g<S, SHIFTED>(f, j * a.plane + k, j);
+            for (int j = 0; j < 9; ++j) g[j] = load_g<S, SHIFTED>(f, j * a.plane + k, j, a.q, sref);
             acc += double(((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8]);
         }
     acc = warp_sum(acc);
@@ -222,10 +255,11 @@ __global__ void __launch_bounds__(kPsiCols) k_psi_seg(FieldArgs a, void* uscr_v,
     const S* f = static_cast<const S*>(a.f);
     C* uscr = static_cast<C*>(uscr_v);
     const int y0 = seg * kPsiSeg, y1 = min(a.ny, y0 + kPsiSeg);
+    const float sref = ref_density<S>(a);
     double s = 0.0;
     for (int y = y0; y < y1; ++y) {
         C drho, u, v;
-        node_moments<S, SHIFTED>(f, a.plane, (long long)y * a.pitch + x, drho, u, v);
+        node_moments<S, SHIFTED>(f, a.plane, (long long)y * a.pitch + x, a.q, sref, drho, u, v);
         uscr[(long long)y * a.nx + x] = u;
         s += double(u);
     }
@@ -311,6 +345,7 @@ size_t psi_scratch_doubles(int nx, int ny) {
         case 2: { using S = float; constexpr bool SH = true; CALL; } break;           \
         case 3: { using S = __half; constexpr bool SH = true; CALL; } break;          \
         case 4: { using S = __nv_bfloat16; constexpr bool SH = true; CALL; } break;   \
+        case 5: { using S = q16; constexpr bool SH = true; CALL; } break;             \
         default: return cudaErrorInvalidValue;                                         \
     }
 

@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) k_batch(const BatchArgs a
             cv.omega = sizeof(C) == 4 ? C(cd.omega_f) : C(cd.omega);
             cv.Ulid = sizeof(C) == 4 ? C(cd.U_f) : C(cd.U);
             cv.corner_moving = cd.corner_moving;
+            cv.sref = cv.sref_w = C(0);  // reference density: LBM_Q16S only, which batches do not take
             ProbeOne pr;
             pr.n_ = (cd.series && !a.no_probe) ? 1 : 0;
             pr.px_ = cd.px;
@@ -650,7 +651,8 @@ extern "C" int lbm_batch_create(int n, const int* nx, const int* ny, const doubl
     };
     if (n < 1 || n > LBM_BATCH_MAX) return bad(bfmt("batch of %d cavities: need 1..%d", n, LBM_BATCH_MAX));
     if (!nx || !ny || !Re || !U) return bad("NULL parameter array");
-    if ((int)dtype < 0 || (int)dtype > 4) return bad("unknown dtype");
+    if ((int)dtype < 0 || (int)dtype > 5) return bad("unknown dtype");
+    if ((int)dtype == kDtypeQ16S) return bad("LBM_Q16S storage is for single cavities only");
     for (int i = 0; i < n; ++i) {
         if (nx[i] < 3 || ny[i] < 3) return bad(bfmt("cavity %d: grid %d x %d, need >= 3", i, nx[i], ny[i]));
         const double tau = 3.0 * U[i] * nx[i] / Re[i] + 0.5;

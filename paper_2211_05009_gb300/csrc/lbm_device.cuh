@@ -50,6 +50,44 @@ template <> struct St<__nv_bfloat16> {
     __device__ static __nv_bfloat16 from(float v) { return __float2bfloat16_rn(v); }
 };
 
+// LBM_Q16S: one 16-bit code per population -- sign, 2-bit exponent E, 13-bit mantissa M -- of
+// h_j / S_j, with h_j = g_j - w_j rho_ref the deviation from the rest state at a reference density
+// 1 + rho_ref (updated at checkpoints) and S_j a power-of-two scale per direction fixed when the
+// context is created.  |h| / S = M 2^-15 for E = 0, (1 + M 2^-13) 2^(E-3) for E = 1..3: 13-bit
+// precision relative to the value over [S/4, 2S), absolute spacing S 2^-15 below.  Codes are
+// converted with integer operations on the FP32 bit pattern: the code's 15 magnitude bits, shifted
+// left by 10, are the FP32 pattern of (|h| / S) 2^-124 (E = 0 gives FP32 subnormals, which the
+// multiply by 2^124 S keeps; the library is built without flush-to-zero).
+struct q16 {
+    unsigned short bits;
+};
+template <> struct St<q16> {
+    static constexpr int V = 8;
+    using C = float;
+};
+
+template <typename S> inline constexpr bool kIsQ16 = false;
+template <> inline constexpr bool kIsQ16<q16> = true;
+
+struct QCodec {
+    float dec[9];  // 2^124 S_j
+    float enc[9];  // 2^-124 / S_j
+};
+
+// code (low 16 bits) -> h
+__device__ __forceinline__ float q16_decode(unsigned code, float dec) {
+    return __uint_as_float(((code & 0x7fffu) << 10) | ((code & 0x8000u) << 16)) * dec;
+}
+// h -> code, round to nearest with ties to even; beyond the largest code (2 - 2^-13) S the
+// magnitude saturates there and *sat becomes true.  NaN saturates too.
+__device__ __forceinline__ unsigned q16_encode(float h, float enc, bool& sat) {
+    const unsigned b = __float_as_uint(h * enc);
+    const unsigned a = b & 0x7fffffffu;
+    const unsigned r = (a + 0x1ffu + ((a >> 10) & 1u)) >> 10;
+    sat |= r > 0x7fffu;
+    return min(r, 0x7fffu) | ((b >> 16) & 0x8000u);
+}
+
 // 16-byte vector load/store of V storage elements, converted to/from C.
 template <typename S>
 __device__ __forceinline__ void vload(const S* __restrict__ p, typename St<S>::C (&out)[St<S>::V]) {
@@ -88,6 +126,11 @@ struct DevState {
     int pad;
     double scalar;        // result of the last on-demand reduction (mass)
     double ext[6];        // stream-function window extrema: min, imin, jmin, max, imax, jmax
+    // LBM_Q16S reference density (rho_ref of the stored deviations): [0] of the current
+    // populations, [1] the one the next checkpoint step stores against (from the last mass)
+    double rho_ref[2];
+    int q16_saturated;    // a checkpoint step stored a population beyond the LBM_Q16S range
+    int pad2;
 };
 
 struct StepArgs {
@@ -105,6 +148,7 @@ struct StepArgs {
     ProbeSet probes;
     void* snap;        // [2][ny][pitch] Eq. 6 velocity snapshot, arithmetic type (REDUCE only)
     double* partials;  // [blocks][3]               (REDUCE only)
+    QCodec q;          // LBM_Q16S scales (unused by the other storage types)
 };
 
 __device__ __forceinline__ double warp_sum(double v) {

@@ -26,9 +26,18 @@ constexpr int kStepConfigs = 6;
 // Fastest shape per storage type measured on GB300 at 2048 x 2048 (f64, f32, f32s, f16s, bf16s);
 // lbm_autotune re-measures on the caller's size.
 inline int default_step_config(int dtype) {
-    constexpr int k[5] = {1, 4, 0, 2, 2};
-    return (dtype >= 0 && dtype < 5) ? k[dtype] : 0;
+    constexpr int k[6] = {1, 4, 0, 2, 2, 2};
+    return (dtype >= 0 && dtype < 6) ? k[dtype] : 0;
 }
+
+constexpr int kDtypeQ16S = 5;
+// LBM_Q16S scale S_j of direction j for lid speed U: the largest code is (2 - 2^-13) S_j, and
+// 2 S_j = the power of two at or above K_j w_j max(|U|, 0.01) with K = 2 (rest), 5 (axes),
+// 11/2 (diagonals), above the largest deviations met in lid-driven cavities from Re 74 to 8000
+// (flat 131 x 13 to 2048^2): |h_j| < 4.5 w_j U (axes), 5.0 w_j U (diagonals), 1.0 w_j U (rest)
+// once the mean density is taken out.
+double q16_scale(int j, double U);
+QCodec q16_codec(double U);
 
 // Geometry of the step launch for a shape (also the number of reduction partials).
 StepGeometry step_geometry(int dtype, int cfg, int ny, long long pitch);
@@ -50,6 +59,8 @@ struct FieldArgs {
     long long pitch, plane;
     double U;
     int corner_moving;
+    QCodec q;              // LBM_Q16S scales
+    const DevState* st;    // LBM_Q16S reference density (rho_ref[0])
 };
 
 // f = f^eq(1, u0) with the Sec. 2.2 (i) initial velocity; snapshot = u0.

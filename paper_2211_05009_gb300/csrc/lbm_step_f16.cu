@@ -11,4 +11,8 @@ cudaError_t launch_step_bf16s(int cfg, const StepArgs& a, bool reduce, cudaStrea
     return launch_step_cfg<__nv_bfloat16, true>(cfg, a, reduce, st);
 }
 
+cudaError_t launch_step_q16s(int cfg, const StepArgs& a, bool reduce, cudaStream_t st) {
+    return launch_step_cfg<q16, true>(cfg, a, reduce, st);
+}
+
 }  // namespace lbm

@@ -163,25 +163,72 @@ __device__ __forceinline__ typename St<S>::C lds(const S* p) {
     }
 }
 
+// One raw 16-bit element with the load path of HINT (see ldg_vec / lds).
+template <int HINT>
+__device__ __forceinline__ unsigned raw16(const void* p) {
+    if constexpr (HINT == 3) {
+        unsigned short r;
+        asm volatile("ld.global.ca.u16 %0, [%1];" : "=h"(r) : "l"(p));
+        return r;
+    } else if constexpr (HINT == 2) {
+        return __ldcg(static_cast<const unsigned short*>(p));
+    } else {
+        return *static_cast<const unsigned short*>(p);
+    }
+}
+
+// One population value in the arithmetic type; qd = the LBM_Q16S decode scale of its direction.
+template <typename S, int HINT>
+__device__ __forceinline__ typename St<S>::C ld1(const S* p, float qd) {
+    if constexpr (kIsQ16<S>) return q16_decode(raw16<HINT>(p), qd);
+    else return lds<S, HINT>(p);
+}
+
+// V values of one direction: load (decoding LBM_Q16S codes with qd) / store (encoding with qe).
+template <typename S, int V, int HINT>
+__device__ __forceinline__ void vload_g(const S* __restrict__ p, float qd, typename St<S>::C (&out)[V]) {
+    if constexpr (kIsQ16<S>) {
+        using T = typename Raw<V * 2>::T;
+        union { T u; unsigned short c[V]; } b;
+        b.u = ldg_vec<T, HINT>(reinterpret_cast<const T*>(p));
+#pragma unroll
+        for (int i = 0; i < V; ++i) out[i] = q16_decode(b.c[i], qd);
+    } else {
+        vload_n<S, V, HINT>(p, out);
+    }
+}
+template <typename S, int V>
+__device__ __forceinline__ void vstore_g(S* __restrict__ p, float qe, const typename St<S>::C (&in)[V], bool& sat) {
+    if constexpr (kIsQ16<S>) {
+        using T = typename Raw<V * 2>::T;
+        union { T u; unsigned short c[V]; } b;
+#pragma unroll
+        for (int i = 0; i < V; ++i) b.c[i] = (unsigned short)q16_encode(in[i], qe, sat);
+        *reinterpret_cast<T*>(p) = b.u;
+    } else {
+        vstore_n<S, V>(p, in);
+    }
+}
+
 // Pull one population row segment: out[i] = value at (x0 + i - DX), DX = c_x of the direction.
 template <typename S, bool SHIFTED, int V, int DX, int HINT>
 __device__ __forceinline__ void pull_row(const S* __restrict__ p, int lane, int x0, long long pitch,
-                                         typename St<S>::C wj, typename St<S>::C (&out)[V]) {
+                                         typename St<S>::C wj, float qd, typename St<S>::C (&out)[V]) {
     using C = typename St<S>::C;
     C v[V];
-    vload_n<S, V, HINT>(p, v);
+    vload_g<S, V, HINT>(p, qd, v);
     if constexpr (DX == 0) {
 #pragma unroll
         for (int i = 0; i < V; ++i) out[i] = v[i];
     } else if constexpr (DX == 1) {
         C left = __shfl_up_sync(kFull, v[V - 1], 1);
-        if (lane == 0) left = (x0 > 0) ? lds<S, HINT>(p - 1) : v[0];
+        if (lane == 0) left = (x0 > 0) ? ld1<S, HINT>(p - 1, qd) : v[0];
         out[0] = left;
 #pragma unroll
         for (int i = 1; i < V; ++i) out[i] = v[i - 1];
     } else {
         C right = __shfl_down_sync(kFull, v[0], 1);
-        if (lane == 31) right = (x0 + V < pitch) ? lds<S, HINT>(p + V) : v[V - 1];
+        if (lane == 31) right = (x0 + V < pitch) ? ld1<S, HINT>(p + V, qd) : v[V - 1];
 #pragma unroll
         for (int i = 0; i < V - 1; ++i) out[i] = v[i + 1];
         out[V - 1] = right;
@@ -210,6 +257,29 @@ __device__ __forceinline__ void geq9(C drho, C rho, C ux, C uy, C (&e)[9]) {
     e[8] = w5 * (drho + rho * A(um));
 }
 
+// BGK collision of a fluid node, f*_j = g_j + omega (g^eq_j - g_j) with g^eq_j = w_j (drho + rho A_j)
+// (Eq. 1, Eq. 2), written per opposite pair (j, jbar): A = c2 +- 3 c.u with c2 = 9/2 (c.u)^2 - usq,
+// so a pair shares c2, drho + rho c2 and 3 rho c.u.  About 50 operations per node instead of the
+// 65 of forming all nine g^eq and then relaxing towards them.  ow = omega w for the three weights.
+template <typename C>
+__device__ __forceinline__ void collide_pairs(C drho, C rho, C ux, C uy, C omega, C ow0, C ow1, C ow5,
+                                              const C (&g)[9], C (&out)[9]) {
+    const C usq = C(1.5) * (ux * ux + uy * uy);
+    const C r3 = C(3.0) * rho;
+    out[0] = fma(ow0, fma(-rho, usq, drho), fma(-omega, g[0], g[0]));
+    auto pair = [&](int a, int b, C cu, C ow) {
+        const C c2 = fma(C(4.5) * cu, cu, -usq);
+        const C base = fma(rho, c2, drho);
+        const C sft = r3 * cu;
+        out[a] = fma(ow, base + sft, fma(-omega, g[a], g[a]));
+        out[b] = fma(ow, base - sft, fma(-omega, g[b], g[b]));
+    };
+    pair(1, 3, ux, ow1);
+    pair(2, 4, uy, ow1);
+    pair(5, 7, ux + uy, ow5);
+    pair(8, 6, ux - uy, ow5);
+}
+
 template <typename C>
 __device__ __forceinline__ C rcp(C v);
 // FP32: hardware reciprocal estimate refined by one Newton-Raphson step r + r(1 - v r) (error
@@ -227,22 +297,22 @@ template <> __device__ __forceinline__ double rcp<double>(double v) { return __d
 // at their inner row, the left/right wall nodes take the populations of x_f = 1 / nx - 2.
 template <typename S, bool SHIFTED, int V, int HINT>
 __device__ __forceinline__ void pull_segment(const S* __restrict__ src, int lane, int x0, int y, int nx,
-                                             int ny, long long pitch, long long plane,
+                                             int ny, long long pitch, long long plane, const QCodec& q,
                                              typename St<S>::C (&f)[9][V]) {
     using C = typename St<S>::C;
     const int yc = min(max(y, 1), ny - 2);  // gather centre row
     const S* pc = src + (long long)yc * pitch + x0;
     const S* ps = pc - pitch;  // row yc - 1: source of c_y = +1
     const S* pn = pc + pitch;  // row yc + 1: source of c_y = -1
-    pull_row<S, SHIFTED, V, 0, HINT>(pc + 0 * plane, lane, x0, pitch, C(4.0 / 9.0), f[0]);
-    pull_row<S, SHIFTED, V, 1, HINT>(pc + 1 * plane, lane, x0, pitch, C(1.0 / 9.0), f[1]);
-    pull_row<S, SHIFTED, V, 0, HINT>(ps + 2 * plane, lane, x0, pitch, C(1.0 / 9.0), f[2]);
-    pull_row<S, SHIFTED, V, -1, HINT>(pc + 3 * plane, lane, x0, pitch, C(1.0 / 9.0), f[3]);
-    pull_row<S, SHIFTED, V, 0, HINT>(pn + 4 * plane, lane, x0, pitch, C(1.0 / 9.0), f[4]);
-    pull_row<S, SHIFTED, V, 1, HINT>(ps + 5 * plane, lane, x0, pitch, C(1.0 / 36.0), f[5]);
-    pull_row<S, SHIFTED, V, -1, HINT>(ps + 6 * plane, lane, x0, pitch, C(1.0 / 36.0), f[6]);
-    pull_row<S, SHIFTED, V, -1, HINT>(pn + 7 * plane, lane, x0, pitch, C(1.0 / 36.0), f[7]);
-    pull_row<S, SHIFTED, V, 1, HINT>(pn + 8 * plane, lane, x0, pitch, C(1.0 / 36.0), f[8]);
+    pull_row<S, SHIFTED, V, 0, HINT>(pc + 0 * plane, lane, x0, pitch, C(4.0 / 9.0), q.dec[0], f[0]);
+    pull_row<S, SHIFTED, V, 1, HINT>(pc + 1 * plane, lane, x0, pitch, C(1.0 / 9.0), q.dec[1], f[1]);
+    pull_row<S, SHIFTED, V, 0, HINT>(ps + 2 * plane, lane, x0, pitch, C(1.0 / 9.0), q.dec[2], f[2]);
+    pull_row<S, SHIFTED, V, -1, HINT>(pc + 3 * plane, lane, x0, pitch, C(1.0 / 9.0), q.dec[3], f[3]);
+    pull_row<S, SHIFTED, V, 0, HINT>(pn + 4 * plane, lane, x0, pitch, C(1.0 / 9.0), q.dec[4], f[4]);
+    pull_row<S, SHIFTED, V, 1, HINT>(ps + 5 * plane, lane, x0, pitch, C(1.0 / 36.0), q.dec[5], f[5]);
+    pull_row<S, SHIFTED, V, -1, HINT>(ps + 6 * plane, lane, x0, pitch, C(1.0 / 36.0), q.dec[6], f[6]);
+    pull_row<S, SHIFTED, V, -1, HINT>(pn + 7 * plane, lane, x0, pitch, C(1.0 / 36.0), q.dec[7], f[7]);
+    pull_row<S, SHIFTED, V, 1, HINT>(pn + 8 * plane, lane, x0, pitch, C(1.0 / 36.0), q.dec[8], f[8]);
     if (x0 == 0) {
 #pragma unroll
         for (int j = 0; j < 9; ++j) f[j][0] = f[j][1];
@@ -258,7 +328,7 @@ __device__ __forceinline__ void pull_segment(const S* __restrict__ src, int lane
         const long long xf = nx - 2;
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
-            const C v = lds<S, HINT>(src + j * plane + (long long)(yc - cy(j)) * pitch + (xf - cx(j)));
+            const C v = ld1<S, HINT>(src + j * plane + (long long)(yc - cy(j)) * pitch + (xf - cx(j)), q.dec[j]);
             f[j][0] = SHIFTED ? v : v - C(wd(j));
         }
     }
@@ -296,6 +366,8 @@ struct CavityView {
     long long pitch, plane;
     C omega, Ulid;
     int corner_moving;
+    QCodec q;        // LBM_Q16S only
+    C sref, sref_w;  // LBM_Q16S only: rho_ref the populations are read against / stored against
 };
 
 // One time step for the V nodes of lane `lane` in row y (x0 = first node): pull, moments,
@@ -314,8 +386,12 @@ __device__ __forceinline__ void step_row(const S* __restrict__ src, S* __restric
     const long long pitch = cv.pitch, plane = cv.plane;
     const C omega = cv.omega;
     const C keep = C(1.0) - omega;  // 1 - 1/tau (wall nodes)
+    const C ow0 = omega * C(4.0 / 9.0), ow1 = omega * C(1.0 / 9.0), ow5 = omega * C(1.0 / 36.0);
     C f[9][V];
-    pull_segment<S, SHIFTED, V, HINT>(src, lane, x0, y, nx, ny, pitch, plane, f);
+    pull_segment<S, SHIFTED, V, HINT>(src, lane, x0, y, nx, ny, pitch, plane, cv.q, f);
+    // LBM_Q16S works on h = g - w rho_ref: BGK and the wall closure keep their form in h with
+    // rho = 1 + rho_ref + sum h (sum w = 1, sum c w = 0); other storage types have rho_ref = 0
+    const C one_ref = kIsQ16<S> ? C(1.0) + cv.sref : C(1.0);
     C sx[V], sy[V];
     if constexpr (REDUCE) {
         cload<C, V, HINT == 2>(snap + (long long)y * pitch + x0, sx);
@@ -338,43 +414,50 @@ __device__ __forceinline__ void step_row(const S* __restrict__ src, S* __restric
 #pragma unroll
         for (int j = 0; j < 9; ++j) g[j] = f[j][i];
         const C drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
-        const C rho = C(1.0) + drho;
+        const C rho = one_ref + drho;
         const C jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
         const C jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
         const C inv = rcp<C>(rho);
         const C ux = jx * inv, uy = jy * inv;
-        C e[9];
-        geq9<C>(drho, rho, ux, uy, e);
         const bool wall = EDGE && ((y == 0) | (y == ny - 1) | (x == 0) | (x >= nx - 1));
         C uox = ux, uoy = uy;
         if (wall) {
             const bool lid = (y == ny - 1) && (cv.corner_moving || (x > 0 && x < nx - 1));
             uox = lid ? cv.Ulid : C(0.0);
             uoy = C(0.0);
-            C ew[9];
+            C e[9], ew[9];
+            geq9<C>(drho, rho, ux, uy, e);
             geq9<C>(drho, rho, uox, uoy, ew);
 #pragma unroll
             for (int j = 0; j < 9; ++j) f[j][i] = ew[j] + keep * (g[j] - e[j]);
-        } else {
-            // BGK as an increment d_j = (f^eq_j - f_j)/tau added to the pulled value.  The
-            // increment must carry no momentum; in FP32 the rounding of f^eq breaks that by a
-            // few ulps in the same direction every step, so the x and y momentum of d is
-            // removed from the (1,3) and (2,4) pairs (a rounding-level change).  With 16-bit
-            // storage the stored rounding (~1e-3 relative) swamps that drift, and the kernel is
-            // issue-bound, so the correction is made for FP32 storage only.
+        } else if constexpr (sizeof(C) == 4 && (sizeof(S) == 4 || kIsQ16<S>)) {
+            // FP32 and LBM_Q16S storage: BGK as an increment d_j = (f^eq_j - f_j)/tau added to
+            // the pulled value.  The increment must carry no momentum; in FP32 the rounding of
+            // f^eq breaks that by a few ulps in the same direction every step, so the x and y
+            // momentum of d is removed from the (1,3) and (2,4) pairs (a rounding-level change).
+            // LBM_Q16S rounds its stores to nearest, which passes such a bias on unchanged on
+            // average, so it needs the correction as much as FP32 storage does.
+            C e[9];
+            geq9<C>(drho, rho, ux, uy, e);
             C d[9];
 #pragma unroll
             for (int j = 0; j < 9; ++j) d[j] = omega * (e[j] - g[j]);
-            if constexpr (sizeof(C) == 4 && sizeof(S) == 4) {
-                const C mx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
-                const C my = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
-                d[1] -= C(0.5) * mx;
-                d[3] += C(0.5) * mx;
-                d[2] -= C(0.5) * my;
-                d[4] += C(0.5) * my;
-            }
+            const C mx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+            const C my = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+            d[1] -= C(0.5) * mx;
+            d[3] += C(0.5) * mx;
+            d[2] -= C(0.5) * my;
+            d[4] += C(0.5) * my;
 #pragma unroll
             for (int j = 0; j < 9; ++j) f[j][i] = g[j] + d[j];
+        } else {
+            // FP64 storage (bound by the FP64 pipe) and binary16 / bfloat16 storage (bound by
+            // instruction issue; their stored rounding swamps an FP32 bias): the pairwise form
+            // with fewer operations.
+            C out[9];
+            collide_pairs<C>(drho, rho, ux, uy, omega, ow0, ow1, ow5, g, out);
+#pragma unroll
+            for (int j = 0; j < 9; ++j) f[j][i] = out[j];
         }
         if (EDGE && x >= nx) {
 #pragma unroll
@@ -383,7 +466,7 @@ __device__ __forceinline__ void step_row(const S* __restrict__ src, S* __restric
         if constexpr (REDUCE) {
             if (!EDGE || x < nx) {
                 const C dx = uox - sx[i], dy = uoy - sy[i];  // exact when close (Sterbenz)
-                acc_drho += drho;
+                acc_drho += kIsQ16<S> ? drho + cv.sref : drho;
                 acc_num += dx * dx + dy * dy;
                 acc_den += sx[i] * sx[i] + sy[i] * sy[i];
             }
@@ -416,13 +499,23 @@ __device__ __forceinline__ void step_row(const S* __restrict__ src, S* __restric
     }
 
     S* pd = dst + (long long)y * pitch + x0;
+    bool sat = false;
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
         if constexpr (!SHIFTED) {
 #pragma unroll
             for (int i = 0; i < V; ++i) f[j][i] += C(wd(j));
         }
-        vstore_n<S, V>(pd + j * plane, f[j]);
+        if constexpr (kIsQ16<S> && REDUCE) {  // re-reference to the next rho_ref
+            const C shift = C(wd(j)) * (cv.sref - cv.sref_w);
+#pragma unroll
+            for (int i = 0; i < V; ++i)
+                if (x0 + i < nx) f[j][i] += shift;
+        }
+        vstore_g<S, V>(pd + j * plane, cv.q.enc[j], f[j], sat);
+    }
+    if constexpr (kIsQ16<S> && REDUCE) {
+        if (sat) acc_num += C(NAN);  // a saturated code: the checkpoint reports non-finite
     }
     if constexpr (REDUCE) {
         cstore<C, V>(snap + (long long)y * pitch + x0, sx);
@@ -465,6 +558,12 @@ __global__ void __launch_bounds__(32 * BY) k_step(const StepArgs a) {
     cv.omega = sizeof(C) == 4 ? C(a.omega_f) : C(a.omega);
     cv.Ulid = sizeof(C) == 4 ? C(a.U_f) : C(a.U);
     cv.corner_moving = a.corner_moving;
+    cv.sref = cv.sref_w = C(0);
+    if constexpr (kIsQ16<S>) {
+        cv.q = a.q;
+        cv.sref = C(__ldcg(&a.state->rho_ref[0]));
+        cv.sref_w = REDUCE ? C(__ldcg(&a.state->rho_ref[1])) : cv.sref;
+    }
     const S* __restrict__ src = static_cast<const S*>(a.src);
     S* __restrict__ dst = static_cast<S*>(a.dst);
     C acc_drho = C(0), acc_num = C(0), acc_den = C(0);

@@ -44,7 +44,7 @@ class GuardedAllocator:
 
 
 @pytest.mark.parametrize("nx,ny,dtype", [(5, 3, "f64"), (33, 9, "f32s"), (7, 130, "f32"), (37, 7, "f16s"),
-                                         (129, 41, "bf16s"), (66, 9, "f64")])
+                                         (129, 41, "bf16s"), (66, 9, "f64"), (131, 13, "q16s")])
 def test_no_write_outside_any_buffer(nx, ny, dtype):
     ga = GuardedAllocator()
     B.lbm_set_allocator(ga.alloc_fn, ga.release_fn)

@@ -3,7 +3,8 @@
 Tolerances (from the accuracy targets of the method's GPU path):
   FP64 storage          max |f_gpu - f_ref| / |f_ref| <= 1e-12 (f >= w_min rho > 0)
   FP32, FP32 shifted    max |u_gpu - u_ref| <= 1e-5 U
-  FP16 / BF16 shifted   max |u_gpu - u_ref| <= 1e-3 U over a short run (reported)
+  16-bit storage        max |u_gpu - u_ref| <= 1e-3 U over a short run (LBM_Q16S, binary16; bfloat16
+                        misses it and is marked as an expected failure with its measured error)
 """
 import os
 import tempfile
@@ -119,8 +120,13 @@ def test_fp32s_rectangular_ar2_re8000():
     assert err <= 1e-5 * 0.1
 
 
-@pytest.mark.parametrize("dtype", ["f16s", "bf16s"])
+@pytest.mark.parametrize("dtype", [
+    "q16s", "f16s",
+    pytest.param("bf16s", marks=pytest.mark.xfail(
+        strict=True, reason="bfloat16 storage misses the 1e-3 U bound: 4.7e-3 U here (and 2.7e-1 U "
+                            "after 2e5 steps of the 2048^2 Re 8000 cavity)"))])
 def test_16bit_storage_velocity_error(dtype):
+    """Reduced-precision storage within 1e-3 U of the FP64 oracle over a short run."""
     nx, ny, Re, steps = 133, 77, 400.0, 300
     p = O.Params.from_re(nx, ny, Re, 0.1)
     with Cavity(nx, ny, Re=Re, U=0.1, dtype=dtype) as cav:
@@ -129,7 +135,7 @@ def test_16bit_storage_velocity_error(dtype):
     _, rr, uxr, uyr = oracle_state(p, steps)
     err = max(np.abs(ux - uxr).max(), np.abs(uy - uyr).max())
     print(f"{dtype} {nx}x{ny} Re={Re} {steps} steps: max|du| = {err / 0.1:.3e} U")
-    assert err <= (1e-3 if dtype == "f16s" else 1e-2) * 0.1
+    assert err <= 1e-3 * 0.1
 
 
 # ---------------------------------------------------------------- arbitrary input fields
