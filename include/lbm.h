@@ -398,8 +398,12 @@ int lbm_net_forward(lbm_net *n, const float *in, int H, int W, float *out);
 int lbm_net_backward(lbm_net *n, const float *in, const float *base, const float *target,
                      const float *mask, int H, int W, double *loss);
 /* GEMM back end of the convolutions: 1 = tcgen05 (default; 5th-generation tensor cores, TMEM
- * accumulator), 0 = mma.sync.  With tcgen05, lbm_net_forward synchronises, and a bounded
- * tensor-core wait that runs out makes forward/backward return LBM_ETIMEOUT. */
+ * accumulator) on an explicit im2col matrix; 2 = tcgen05 with the forward and data-gradient
+ * products as implicit GEMMs (the im2col rows are gathered inside the kernel,
+ * lbm_nn_conv3x3_bf16_tc05; bitwise the same results as 1, a fifth of the DRAM traffic, but
+ * slower: its gather is bound by instruction issue); 0 = mma.sync.  With tcgen05, lbm_net_forward
+ * synchronises, and a bounded tensor-core wait that runs out makes forward/backward return
+ * LBM_ETIMEOUT. */
 int lbm_net_set_backend(lbm_net *n, int backend);
 /* One Adam step on the accumulated gradient times grad_scale (e.g. 1/batch). */
 int lbm_net_adam_step(lbm_net *n, float lr, float beta1, float beta2, float eps, float grad_scale);
@@ -441,6 +445,18 @@ int lbm_nn_gemm_bf16(int M, int N, int K, const void *A, int lda, const void *B,
  * (the result is then incomplete).  Asynchronous. */
 int lbm_nn_gemm_bf16_tc05(int M, int N, int K, const void *A, int lda, const void *B, int ldb,
                           float *C, int ldc, int op, int trans_c, int split_k, int *err, void *stream);
+
+/* 3x3 convolution (padding 1) of the FP32 inputs x1 [c1][H][W] ++ x2 [c2][H][W] (x2 may be NULL
+ * with c2 = 0) as an implicit GEMM on the tcgen05 tensor cores: C[p][n] (op)= sum_k A[p][k] Wt[n][k]
+ * with A the pixel-major im2col, k = ci*9 + ky*3 + kx, zeros outside the image and past
+ * (c1 + c2)*9, each value rounded to BF16; A is never written to memory (each thread gathers one
+ * pixel row of a 128 x 64 tile into shared memory).  Wt: DEVICE [N][K] BF16, K a multiple of 8 and
+ * >= (c1 + c2)*9, 16-byte aligned; N <= 256.  C, op, trans_c, err as lbm_nn_gemm_bf16_tc05 with
+ * M = H*W.  Bitwise equal to that GEMM on the explicit im2col.  No counterpart in the paper (the
+ * warm start's convolutions).  Asynchronous.  Errors: LBM_EINVAL (shapes, NULL), LBM_ECUDA. */
+int lbm_nn_conv3x3_bf16_tc05(const float *x1, int c1, const float *x2, int c2, int H, int W, int K,
+                             const void *Wt, int N, float *C, int ldc, int op, int trans_c, int *err,
+                             void *stream);
 
 /* ------------------------------------------------------------------ checkpoint */
 

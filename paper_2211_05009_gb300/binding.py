@@ -118,6 +118,7 @@ _SIGS = [
     ("lbm_nn_gemm_bf16", _I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _I, _P]),
     ("lbm_nn_gemm_bf16_tc05", _I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _I, _I, _P, _P]),
     ("lbm_fma_peak", _I, [_I, _I, _DP, _DP]),
+    ("lbm_nn_conv3x3_bf16_tc05", _I, [_P, _I, _P, _I, _I, _I, _I, _P, _I, _P, _I, _I, _I, _P, _P]),
     ("lbm_save", _I, [_P, ctypes.c_char_p]),
     ("lbm_load", _I, [_P, ctypes.c_char_p]),
 ]
@@ -530,6 +531,11 @@ def lbm_warm_target(rho, ux, uy, nx, ny, H, U, target, stream_handle=None) -> No
 
 def lbm_nn_gemm_bf16(M, N, K, A, lda, B, ldb, C, ldc, op=0, split_k=1, stream_handle=None) -> int:
     return library().lbm_nn_gemm_bf16(M, N, K, _tptr(A), lda, _tptr(B), ldb, _tptr(C), ldc, op, split_k, stream_handle)
+
+
+def lbm_nn_conv3x3_bf16_tc05(x1, c1, x2, c2, H, W, K, Wt, N, C, ldc, op, err, trans_c=0, stream_handle=None) -> int:
+    return library().lbm_nn_conv3x3_bf16_tc05(_tptr(x1), c1, _tptr(x2) if x2 is not None else None, c2, H, W, K,
+                                              _tptr(Wt), N, _tptr(C), ldc, op, trans_c, _tptr(err), stream_handle)
 
 
 def lbm_nn_gemm_bf16_tc05(M, N, K, A, lda, B, ldb, C, ldc, op, err, trans_c=0, split_k=1, stream_handle=None) -> int:

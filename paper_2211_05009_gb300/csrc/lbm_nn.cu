@@ -353,7 +353,7 @@ struct lbm_net {
     double* d_loss = nullptr;
     double* h_loss = nullptr;
     int* d_err = nullptr;          // set by a tcgen05 GEMM whose bounded wait ran out
-    int backend = 1;               // 0: mma.sync GEMM, 1: tcgen05 GEMM
+    int backend = 1;               // 0: mma.sync GEMM, 1: im2col + tcgen05 GEMM, 2: tcgen05 implicit conv
     cudaStream_t stream = nullptr;
     std::string err;
 
@@ -489,10 +489,20 @@ int prep_weights(lbm_net* n) {
 // y (tensor) = act(conv(x1 ++ x2) + b)
 int conv_fwd(lbm_net* n, const ConvSpec& c, const float* x1, int c1, const float* x2, int c2, int H, int W, float* y) {
     const long long P = (long long)H * W;
-    k_im2col_pk<<<nblk(P * c.Kp), 256, 0, n->stream>>>(x1, c1, x2, c2, H, W, c.Kp, n->col);
-    int rc = n->cuda(cudaGetLastError(), "im2col");
-    if (!rc) {
-        if (n->backend == 1)  // pixels on the 128-row side, channels on N, stored transposed
+    int rc = LBM_OK;
+    bool implicit = n->backend == 2;
+    if (implicit) {  // implicit GEMM: the im2col rows are gathered inside the tensor-core kernel
+        const cudaError_t e = conv3x3_bf16_umma(x1, c1, x2, c2, H, W, c.Kp, n->wq + c.wq_off, c.co, y, (int)P, kStore,
+                                                true, n->d_err, n->stream);
+        if (e == cudaErrorInvalidValue) implicit = false;  // shape it does not take: explicit im2col below
+        else rc = n->cuda(e, "conv (tcgen05 implicit)");
+    }
+    if (!implicit) {
+        k_im2col_pk<<<nblk(P * c.Kp), 256, 0, n->stream>>>(x1, c1, x2, c2, H, W, c.Kp, n->col);
+        rc = n->cuda(cudaGetLastError(), "im2col");
+    }
+    if (!rc && !implicit) {
+        if (n->backend != 0)  // pixels on the 128-row side, channels on N, stored transposed
             rc = n->cuda(gemm_bf16_nt_umma((int)P, c.co, c.Kp, n->col, c.Kp, n->wq + c.wq_off, c.Kp, y, (int)P, kStore, true, 1,
                                            n->d_err, n->stream), "conv gemm (tcgen05)");
         else
@@ -521,7 +531,7 @@ int conv_bwd(lbm_net* n, const ConvSpec& c, const float* x1, int c1, const float
     }
     if (!rc) {
         const int split = P >= 16384 ? (int)std::min<long long>(32, P / 4096) : 1;
-        if (n->backend == 1)  // rows k of the k-major im2col on the 128-row side, co on N
+        if (n->backend != 0)  // rows k of the k-major im2col on the 128-row side, co on N
             rc = n->cuda(gemm_bf16_nt_umma(c.ci * 9, c.co, (int)P, n->col, (int)P, n->dzq, (int)P, n->grads + c.woff, c.ci * 9,
                                            kAtomicAdd, true, split, n->d_err, n->stream), "weight-gradient gemm (tcgen05)");
         else
@@ -530,18 +540,34 @@ int conv_bwd(lbm_net* n, const ConvSpec& c, const float* x1, int c1, const float
     }
     // data gradient: dX[ci][p] = sum_k Wf[ci][k] dZc[p][k]
     if (!rc && (gx1 || gx2)) {
-        k_im2col_pk<<<nblk(P * c.Kp2), 256, 0, n->stream>>>(n->dz, c.co, nullptr, 0, H, W, c.Kp2, n->col);
-        rc = n->cuda(cudaGetLastError(), "im2col of dZ");
         const __nv_bfloat16* wf1 = n->wf + c.wf_off;
         const __nv_bfloat16* wf2 = wf1 + (long long)c1 * c.Kp2;
-        if (n->backend == 1) {
+        bool implicit = n->backend == 2;
+        if (implicit) {  // implicit GEMM over dZ (co channels) with the flipped weights
+            bool first = true;  // a shape the kernel does not take is refused before anything launches
+            for (int part = 0; part < 2 && !rc && implicit; ++part) {
+                float* gx = part == 0 ? gx1 : gx2;
+                if (!gx) continue;
+                const cudaError_t e = conv3x3_bf16_umma(n->dz, c.co, nullptr, 0, H, W, c.Kp2, part == 0 ? wf1 : wf2,
+                                                        part == 0 ? c1 : c2, gx, (int)P, kAccumulate, true, n->d_err,
+                                                        n->stream);
+                if (e == cudaErrorInvalidValue && first) implicit = false;  // explicit im2col below
+                else rc = n->cuda(e, "data-gradient conv (tcgen05 implicit)");
+                first = false;
+            }
+        }
+        if (!implicit) {
+            k_im2col_pk<<<nblk(P * c.Kp2), 256, 0, n->stream>>>(n->dz, c.co, nullptr, 0, H, W, c.Kp2, n->col);
+            rc = n->cuda(cudaGetLastError(), "im2col of dZ");
+        }
+        if (!implicit && n->backend != 0) {
             if (!rc && gx1)
                 rc = n->cuda(gemm_bf16_nt_umma((int)P, c1, c.Kp2, n->col, c.Kp2, wf1, c.Kp2, gx1, (int)P, kAccumulate, true, 1,
                                                n->d_err, n->stream), "data-gradient gemm (tcgen05)");
             if (!rc && gx2)
                 rc = n->cuda(gemm_bf16_nt_umma((int)P, c2, c.Kp2, n->col, c.Kp2, wf2, c.Kp2, gx2, (int)P, kAccumulate, true, 1,
                                                n->d_err, n->stream), "data-gradient gemm (tcgen05)");
-        } else {
+        } else if (n->backend == 0) {
             if (!rc && gx1)
                 rc = n->cuda(gemm_bf16_nt(c1, (int)P, c.Kp2, wf1, c.Kp2, n->col, c.Kp2, gx1, (int)P, kAccumulate, 1, n->stream),
                              "data-gradient gemm");
@@ -740,7 +766,7 @@ static int check_err(lbm_net* n) {
 }
 
 extern "C" int lbm_net_set_backend(lbm_net* n, int backend) {
-    if (!n || backend < 0 || backend > 1) return LBM_EINVAL;
+    if (!n || backend < 0 || backend > 2) return LBM_EINVAL;
     n->backend = backend;
     return LBM_OK;
 }
@@ -761,7 +787,7 @@ extern "C" int lbm_net_forward(lbm_net* n, const float* in, int H, int W, float*
         Graph g = make_graph(n->ch);
         rc = n->cuda(cudaMemcpyAsync(out, n->act[g.out], n->act_size[g.out] * 4, cudaMemcpyDeviceToDevice, n->stream), "output copy");
     }
-    if (!rc && n->backend == 1) {
+    if (!rc && n->backend != 0) {
         rc = n->cuda(cudaStreamSynchronize(n->stream), "stream synchronize");
         if (!rc) rc = check_err(n);
     }
@@ -872,6 +898,16 @@ extern "C" int lbm_nn_gemm_bf16(int M, int N, int K, const void* A, int lda, con
     const cudaError_t e = gemm_bf16_nt(M, N, K, static_cast<const __nv_bfloat16*>(A), lda,
                                        static_cast<const __nv_bfloat16*>(B), ldb, C, ldc, (GemmOp)op, split_k,
                                        (cudaStream_t)stream);
+    if (e == cudaErrorInvalidValue) return LBM_EINVAL;
+    return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
+
+extern "C" int lbm_nn_conv3x3_bf16_tc05(const float* x1, int c1, const float* x2, int c2, int H, int W, int K,
+                                        const void* Wt, int N, float* C, int ldc, int op, int trans_c, int* err,
+                                        void* stream) {
+    if (!x1 || !Wt || !C || !err || op < 0 || op > 2 || H < 1 || W < 1) return LBM_EINVAL;
+    const cudaError_t e = conv3x3_bf16_umma(x1, c1, x2, c2, H, W, K, static_cast<const __nv_bfloat16*>(Wt), N, C, ldc,
+                                            (GemmOp)op, trans_c != 0, err, (cudaStream_t)stream);
     if (e == cudaErrorInvalidValue) return LBM_EINVAL;
     return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }

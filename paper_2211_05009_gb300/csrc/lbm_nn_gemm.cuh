@@ -30,5 +30,14 @@ cudaError_t gemm_bf16_nt_umma(int M, int N, int K, const __nv_bfloat16* A, int l
                               const __nv_bfloat16* B, int ldb, float* C, int ldc, GemmOp op, bool trans_c,
                               int split_k, int* err, cudaStream_t st);
 
+// C = conv3x3(x1 ++ x2) as the same product with A = the pixel-major im2col (k = ci*9 + ky*3 + kx,
+// padding 1, zeros past (c1 + c2)*9), gathered on the fly from the FP32 [C][H][W] inputs and
+// rounded to BF16 exactly as the explicit im2col does (so the result is bitwise that of
+// im2col + gemm_bf16_nt_umma).  M = H*W pixels, Wt = [N][K] BF16 weights (K a multiple of 8,
+// >= (c1 + c2)*9), N <= 256.
+cudaError_t conv3x3_bf16_umma(const float* x1, int c1, const float* x2, int c2, int H, int W, int K,
+                              const __nv_bfloat16* Wt, int N, float* C, int ldc, GemmOp op, bool trans_c, int* err,
+                              cudaStream_t st);
+
 }  // namespace nn
 }  // namespace lbm

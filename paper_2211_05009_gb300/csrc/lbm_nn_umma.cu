@@ -219,6 +219,246 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 2) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((uint32_t)cols));
 }
 
+// ------------------------------------------------------------------ implicit-GEMM convolution
+// The same product with A = the pixel-major im2col of a 3x3, padding-1 convolution input, never
+// written to memory.  Per 64-wide K step the CTA first copies, with coalesced loads, the input
+// window its 128 pixels need -- the (at most 8) channels of that K range, the tile's pixel rows
+// plus one halo row above and below, the tile's columns plus one halo column each side, zeros
+// outside the image -- into shared memory; then every thread builds one row (pixel) of the
+// 128 x 64 A stage from that window (k = ci*9 + ky*3 + kx, zeros past C*9), rounds it to BF16
+// exactly as the explicit im2col does, and writes it in the 128-byte swizzle layout (16-byte
+// chunk c of row r at r*128 + ((c ^ (r & 7)) * 16)).  B (the weights) still arrives by TMA.  The
+// "full" barrier of a stage takes 128 thread arrivals (each after a proxy fence, so the tensor
+// cores see the generic-proxy stores) plus the TMA's.  The CTA moves through the K steps together
+// (block barriers around the window), and every decision to stop is taken block-wide.
+struct ConvIn {
+    const float* x1;
+    const float* x2;
+    int c1, c2, H, W;
+    int win_floats;  // per-channel window capacity (floats) the launch reserved
+};
+
+constexpr int kWinCh = 8;  // channels a 64-wide K range can touch (ceil(64 / 9) + 1)
+
+__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// Window geometry of the tile starting at pixel m0: rows wy0 .. wy0+R-1, columns wx0 .. wx0+WC-1.
+__host__ __device__ inline void conv_window(int m0, int M, int W, int TMr, int& wy0, int& R, int& wx0, int& WC) {
+    const int pend = (m0 + TMr < M ? m0 + TMr : M);
+    const int py0 = m0 / W, py1 = (pend - 1) / W;
+    wy0 = py0 - 1;
+    R = py1 - py0 + 3;
+    if (py0 == py1) {
+        wx0 = m0 % W - 1;
+        WC = pend - m0 + 2;
+    } else {
+        wx0 = -1;
+        WC = W + 2;
+    }
+}
+
+constexpr int kConvThreads = 256;  // two threads per A row (32 K values each)
+
+__global__ void __launch_bounds__(kConvThreads, 2)
+    k_conv_tc05(const ConvIn in, const __grid_constant__ CUtensorMap tmB, int N, int K, float* __restrict__ C,
+                int ldc, int op, int trans_c, int tn, int cols, int stages, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int stage_bytes = kTileA + tn * TK * 2;
+    // two input windows (step t and the prefetch of t+1), each [kWinCh][win_floats] + a zero slot
+    const int win_stride = kWinCh * in.win_floats + 4;
+    float* win_base = reinterpret_cast<float*>(base + (size_t)stages * stage_bytes);
+    uint64_t* full = reinterpret_cast<uint64_t*>(win_base + 2 * (size_t)win_stride);
+    uint64_t* empty = full + stages;
+    uint64_t* done = empty + stages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    __shared__ volatile int abort_flag;
+    __shared__ int koff[TK];  // window offset of each K value of the step (from a pixel's corner; -1: zero)
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long P = (long long)in.H * in.W;
+    const int M = (int)P, W = in.W;
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * tn;
+    const int nk = (K + TK - 1) / TK;
+    const int C_in = in.c1 + in.c2, CK = C_in * 9;
+    const int zero_slot = kWinCh * in.win_floats;  // always 0: read for K values past C*9
+    auto sA = [&](int s) { return sa(base + (size_t)s * stage_bytes); };
+    auto sB = [&](int s) { return sa(base + (size_t)s * stage_bytes + kTileA); };
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        win_base[zero_slot] = 0.f;
+        win_base[win_stride + zero_slot] = 0.f;
+        for (int s = 0; s < stages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(sa(&full[s])), "r"(kConvThreads + 1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sa(&empty[s])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sa(done)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(sa(tmem_slot)), "r"((uint32_t)cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    const uint32_t tmem = *tmem_slot;
+    if (threadIdx.x == 0) asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+
+    int wy0, R, wx0, WC;
+    conv_window(m0, M, W, TM, wy0, R, wx0, WC);
+    // this thread's pixel (row of A), half of the K step, and its 3x3 corner in the window
+    const int r = threadIdx.x & (TM - 1), half = threadIdx.x >> 7;
+    const int pm = m0 + r;
+    const bool row_ok = pm < M;
+    const int off0 = row_ok ? (pm / W - 1 - wy0) * WC + (pm % W - 1 - wx0) : 0;
+    const bool issuer = threadIdx.x == 32;  // warp 1, lane 0
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(tn >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+    // asynchronous copy (cp.async, 4 bytes, zero fill outside the image) of the input window of
+    // the channels K step tt touches into window buffer tt & 1
+    auto load_window = [&](int tt) {
+        const int kk0 = tt * TK, c0 = kk0 / 9;
+        const int nch = min(C_in, (kk0 + TK + 8) / 9) - c0;
+        float* wb = win_base + (size_t)(tt & 1) * win_stride;
+        for (int q = 0; q < nch * R; ++q) {  // window rows, channel-major
+            const int c = q / R, wy = q - c * R;
+            const int ci = c0 + c, y = wy0 + wy;
+            const float* src = ci < in.c1 ? in.x1 + (long long)ci * P : in.x2 + (long long)(ci - in.c1) * P;
+            const bool yin = y >= 0 && y < in.H;
+            for (int wx = threadIdx.x; wx < WC; wx += kConvThreads) {
+                const int x = wx0 + wx;
+                const bool inside = yin && x >= 0 && x < W;
+                const float* g = inside ? src + (long long)y * W + x : in.x1;  // any valid address when empty
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa(wb + (size_t)c * in.win_floats + wy * WC + wx)),
+                             "l"(g), "r"(inside ? 4 : 0)
+                             : "memory");
+            }
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    if (nk > 0) load_window(0);
+    int t = 0;
+    for (; t < nk; ++t) {
+        const int s = t % stages;
+        // the stage is free once the MMAs of t - stages completed (thread 0 waits; the block
+        // barrier passes the news on, and any failure stops every thread at the same point)
+        bool bad = false;
+        if (threadIdx.x == 0 && t >= stages) bad = !mbar_wait(sa(&empty[s]), ((t / stages) - 1) & 1, nullptr);
+        if (__syncthreads_or(bad || abort_flag)) {
+            if (threadIdx.x == 0) abort_flag = 1;
+            break;
+        }
+        const int k0 = t * TK;
+        const int ci0 = k0 / 9;
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(sa(&full[s])), "r"(tn * TK * 2)
+                         : "memory");
+            tma_load_2d(sB(s), &tmB, k0, n0, sa(&full[s]));
+        }
+        if (threadIdx.x < TK) {  // offsets of k0 .. k0+63 in the window; past C*9 the zero slot
+            const int k = k0 + threadIdx.x;
+            const int cl = k / 9 - ci0, tap = k % 9, ky = tap / 3;
+            koff[threadIdx.x] = k < CK ? cl * in.win_floats + ky * WC + (tap - 3 * ky) : -1;
+        }
+        // this step's window (copied during the previous step) is in; then start the next one
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        __syncthreads();
+        if (t + 1 < nk) load_window(t + 1);
+        const float* win = win_base + (size_t)(t & 1) * win_stride;
+        // this thread's 32 K values of row r
+        uint32_t w[16];
+#pragma unroll
+        for (int j2 = 0; j2 < 16; ++j2) {
+            const int j = half * 32 + 2 * j2;
+            const int kf0 = koff[j], kf1 = koff[j + 1];
+            // off0 + kf stays inside the window (kf <= 7 win_floats + 2 WC + 2, off0 <= (R-3) WC + WC-3);
+            // K values past C*9 and pixels past the image read the zero slot
+            const float lo = win[(row_ok && kf0 >= 0) ? off0 + kf0 : zero_slot];
+            const float hi = win[(row_ok && kf1 >= 0) ? off0 + kf1 : zero_slot];
+            w[j2] = bf16x2(lo, hi);
+        }
+        unsigned char* rowp = base + (size_t)s * stage_bytes + (size_t)r * 128;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int chunk = half * 4 + c;
+            *reinterpret_cast<uint4*>(rowp + ((chunk ^ (r & 7)) << 4)) =
+                make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(sa(&full[s])) : "memory");
+        if (issuer) {
+            // MMA issuer: stage t once all rows and the weight tile are in
+            if (!mbar_wait(sa(&full[s]), (t / stages) & 1, nullptr)) {
+                abort_flag = 1;  // the next block-wide check stops everyone
+            } else {
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+#pragma unroll
+                for (int kk = 0; kk < TK / 16; ++kk) {
+                    const uint64_t da = desc_sw128(sA(s) + kk * 32);
+                    const uint64_t db = desc_sw128(sB(s) + kk * 32);
+                    const uint32_t acc = (t > 0 || kk > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(da), "l"(db), "r"(idesc), "r"(acc));
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(sa(&empty[s])));
+            }
+        }
+    }
+    if (issuer)  // arrives once every MMA issued above has completed (at once if none was issued)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(sa(done)));
+    if (threadIdx.x == 0 && abort_flag) {
+        // weight copies already issued must land before the CTA may leave (bounded waits)
+        for (int u = t > stages ? t - stages : 0; u < t; ++u) mbar_wait(sa(&full[u % stages]), (u / stages) & 1, nullptr);
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");  // a window prefetch in flight after an early stop
+    __syncwarp();
+
+    // epilogue, as in k_gemm_tc05, by warps 0..3 (TMEM lanes 32w .. 32w+31)
+    const bool fin = mbar_wait(sa(done), 0, nullptr);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    if (warp < 4 && fin && !abort_flag && nk > 0) {
+        const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < tn; c0 += 16) {
+            uint32_t v[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15}, [%16];\n"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+            if (row < M) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int n = n0 + c0 + j;
+                    if (n < N) {
+                        float* c = trans_c ? C + (long long)n * ldc + row : C + (long long)row * ldc + n;
+                        const float f = __uint_as_float(v[j]);
+                        if (op == kAtomicAdd)
+                            atomicAdd(c, f);
+                        else if (op == kAccumulate)
+                            *c += f;
+                        else
+                            *c = f;
+                    }
+                }
+            }
+        }
+    }
+    if (threadIdx.x == 0 && (!fin || abort_flag)) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    if (warp == 2) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((uint32_t)cols));
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
@@ -281,6 +521,51 @@ cudaError_t gemm_bf16_nt_umma(int M, int N, int K, const __nv_bfloat16* A, int l
     const dim3 grid(p.tiles_n, (M + TM - 1) / TM, split_k);
     k_gemm_tc05<<<grid, 128, p.smem, st>>>(ma, mb, M, N, K, C, ldc, (int)op, trans_c ? 1 : 0, kps, p.tn, p.cols,
                                             p.stages, err);
+    return cudaGetLastError();
+}
+
+cudaError_t conv3x3_bf16_umma(const float* x1, int c1, const float* x2, int c2, int H, int W, int K,
+                              const __nv_bfloat16* Wt, int N, float* C, int ldc, GemmOp op, bool trans_c, int* err,
+                              cudaStream_t st) {
+    const long long P = (long long)H * W;
+    if (P <= 0 || N <= 0) return cudaSuccess;
+    if (!x1 || c1 < 1 || c2 < 0 || (c2 > 0 && !x2) || P > 0x7fffffffll) return cudaErrorInvalidValue;
+    if ((K & 7) || K < (c1 + c2) * 9 || !err || ((uintptr_t)Wt & 15)) return cudaErrorInvalidValue;
+    Plan p = plan_for(N);
+    if (p.tiles_n != 1 || p.tn > 256) return cudaErrorInvalidValue;  // one N tile (N <= 256)
+    // the largest input window over the tiles (floats per channel), and the stage ring that fits
+    // beside it in the per-CTA budget (two CTAs per SM)
+    int win = 0;
+    for (long long m0 = 0; m0 < P; m0 += TM) {
+        int wy0, R, wx0, WC;
+        conv_window((int)m0, (int)P, W, TM, wy0, R, wx0, WC);
+        win = R * WC > win ? R * WC : win;
+    }
+    win = (win + 3) / 4 * 4;
+    const int win_bytes = 2 * (kWinCh * win + 4) * 4;  // two windows, each with its zero slot
+    const int stage = kTileA + p.tn * TK * 2;
+    p.stages = (kSmemBudget - kSmemExtra - win_bytes) / stage;
+    if (p.stages > 6) p.stages = 6;
+    if (p.stages < 2) return cudaErrorInvalidValue;  // window too wide for the budget: use the explicit im2col
+    p.smem = p.stages * stage + win_bytes + kSmemExtra;
+    CUtensorMap mb;
+    if (!make_map(&mb, Wt, N, K, K, p.tn)) return cudaErrorInvalidValue;
+    {
+        static std::mutex mu;
+        static int opted[64] = {};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        std::lock_guard<std::mutex> lock(mu);
+        if (dev >= 64 || p.smem > opted[dev]) {
+            e = cudaFuncSetAttribute(k_conv_tc05, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
+            if (e != cudaSuccess) return e;
+            if (dev < 64) opted[dev] = p.smem;
+        }
+    }
+    const ConvIn in{x1, x2, c1, c2, H, W, win};
+    const dim3 grid(1, (unsigned)((P + TM - 1) / TM), 1);
+    k_conv_tc05<<<grid, kConvThreads, p.smem, st>>>(in, mb, N, K, C, ldc, (int)op, trans_c ? 1 : 0, p.tn, p.cols, p.stages, err);
     return cudaGetLastError();
 }
 

@@ -232,3 +232,66 @@ def test_gemm_tcgen05_strided_operands_ignore_the_padding():
     got = C.cpu().numpy()
     assert np.isfinite(got).all()
     assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-5
+
+
+def _im2col_pk(x, H, W, K):
+    """Pixel-major im2col from its definition: row p = y*W + x, column k = ci*9 + ky*3 + kx,
+    padding 1, zeros past C*9 (numpy, float64)."""
+    C = x.shape[0]
+    xp = np.zeros((C, H + 2, W + 2))
+    xp[:, 1:-1, 1:-1] = x
+    out = np.zeros((H * W, K))
+    for ci in range(C):
+        for ky in range(3):
+            for kx in range(3):
+                out[:, ci * 9 + ky * 3 + kx] = xp[ci, ky:ky + H, kx:kx + W].reshape(-1)
+    return out
+
+
+@pytest.mark.parametrize("c1,c2,H,W,N", [(3, 0, 16, 40, 20), (7, 5, 33, 9, 40), (20, 20, 64, 64, 160),
+                                         (1, 0, 5, 3, 16), (40, 0, 24, 24, 72)])
+def test_implicit_conv_equals_explicit_im2col_gemm(c1, c2, H, W, N):
+    """lbm_nn_conv3x3_bf16_tc05 (im2col rows gathered inside the kernel) is bitwise the tcgen05
+    GEMM on the explicit im2col of the same inputs, and within 1e-5 of the FP64 convolution of the
+    BF16-rounded operands."""
+    g = torch.Generator(device="cpu").manual_seed(c1 * 100 + H)
+    C = c1 + c2
+    K = (C * 9 + 7) // 8 * 8
+    x = torch.randn(C, H, W, generator=g)
+    Wt = torch.randn(N, K, generator=g).to(torch.bfloat16)
+    Wt[:, C * 9:] = 0
+    x1 = x[:c1].contiguous().cuda()
+    x2 = x[c1:].contiguous().cuda() if c2 else None
+    Wd = Wt.cuda()
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    P = H * W
+    out = torch.full((N, P), float("nan"), dtype=torch.float32, device="cuda")
+    assert B.lbm_nn_conv3x3_bf16_tc05(x1, c1, x2, c2, H, W, K, Wd, N, out, P, 0, err, trans_c=1) == B.LBM_OK
+    A = torch.tensor(_im2col_pk(x.double().numpy(), H, W, K)).to(torch.bfloat16)
+    ref_c = torch.full((N, P), float("nan"), dtype=torch.float32, device="cuda")
+    assert B.lbm_nn_gemm_bf16_tc05(P, N, K, A.cuda().contiguous(), K, Wd, K, ref_c, P, 0, err, 1, 1) == B.LBM_OK
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    assert torch.equal(out, ref_c)
+    ref = (A.double().numpy() @ Wt.double().numpy().T).T
+    assert np.abs(out.cpu().numpy() - ref).max() / np.abs(ref).max() < 1e-5
+
+
+def test_network_implicit_and_explicit_backends_agree():
+    """The network's forward output and gradients with the implicit convolutions (backend 2) are
+    bitwise those with explicit im2col (backend 1)."""
+    H, W = 64, 128
+    res = []
+    for backend in (1, 2):
+        n, p, arrs, (dx, dbase, dtgt, dmask) = _setup(H=H, W=W, backend=backend)
+        try:
+            out = torch.empty((3, H, W), dtype=torch.float32, device="cuda")
+            B.lbm_net_forward(n, dx, H, W, out)
+            B.lbm_net_zero_grads(n)
+            loss = B.lbm_net_backward(n, dx, dbase, dtgt, dmask, H, W)
+            g = torch.empty(B.lbm_net_param_count(n), dtype=torch.float32, device="cuda")
+            B.lbm_net_get_grads(n, g)
+            res.append((out.cpu(), loss, g.cpu()))
+        finally:
+            B.lbm_net_destroy(n)
+    assert torch.equal(res[0][0], res[1][0]) and res[0][1] == res[1][1] and torch.equal(res[0][2], res[1][2])
