@@ -67,6 +67,7 @@ struct BatchState {
     int n_active;
     int err;         // 1: a barrier wait ran out
     unsigned bar_count, bar_gen;
+    unsigned claim;  // work-item tickets drawn in the current launch (0 between launches)
     double tol;          // retire when residual < tol (tol <= 0: never)
     long long max_step;  // retire a cavity at this global step (<= 0: never)
     int active[LBM_BATCH_MAX];
@@ -137,15 +138,13 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) k_batch(const BatchArgs a
     __shared__ int s_n;
     BatchState* st = a.st;
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
     constexpr int W = kBatchThreads / 32;
-    const long long gwarp = (long long)blockIdx.x * W + warp;
-    const long long nwarps = (long long)gridDim.x * W;
+    const unsigned nwarps = gridDim.x * W;
     const long long step0 = __ldcg(&st->step);
+    unsigned ticket0 = 0;  // the claim counter's value at the start of the current step
 
     for (int s = 0; s < a.nsteps; ++s) {
         const long long step = step0 + s;
-        constexpr bool reduce = REDUCE;
         // the active list (changes only at checkpoints, behind barriers)
         if (threadIdx.x == 0) s_n = __ldcg(&st->n_active);
         __syncthreads();
@@ -161,11 +160,21 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) k_batch(const BatchArgs a
         const bool odd = (step & 1) != 0;
         const S* src_pool = static_cast<const S*>(odd ? a.pool[1] : a.pool[0]);
         S* dst_pool = static_cast<S*>(odd ? a.pool[0] : a.pool[1]);
-        for (long long item = gwarp; item < n_items; item += nwarps) {
+        // Work items are drawn one at a time from a grid-wide ticket counter, so that a warp which
+        // drew cheaper items (interior strips, no wall path) takes more of them; a static
+        // round-robin gave every warp the same strip of every cavity whenever the warp count was
+        // a multiple of the strips per row.  The next ticket is drawn during the item's last row,
+        // which hides the atomic's latency.  Each warp draws exactly one ticket past the end per
+        // step, so a step consumes n_items + nwarps tickets.
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(&st->claim, 1u);
+        // unsigned: a counter left over from an aborted launch can only skip items, never index below 0
+        unsigned item = __shfl_sync(kFull, t, 0) - ticket0;
+        while (item < (unsigned)n_items) {
             int lo = 0, hi = n - 1;  // largest k with prefix[k] <= item
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (s_prefix[mid] <= item) lo = mid; else hi = mid - 1;
+                if ((unsigned)s_prefix[mid] <= item) lo = mid; else hi = mid - 1;
             }
             const BatchCav& cd = a.cavs[s_active[lo]];
             const int local = (int)(item - s_prefix[lo]);
@@ -192,10 +201,12 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) k_batch(const BatchArgs a
             C* snap = static_cast<C*>(a.snap) + cd.snap_off;
             const int x0 = (strip * 32 + lane) * V;
             C a0 = C(0), a1 = C(0), a2 = C(0);
+            unsigned next = 0;
 #pragma unroll 1
             for (int r = 0; r < a.rows; ++r) {
                 const int y = rg * a.rows + r;
                 if (y >= cd.ny) break;
+                if (lane == 0 && (r == a.rows - 1 || y + 1 == cd.ny)) next = atomicAdd(&st->claim, 1u);
                 step_row<S, SHIFTED, REDUCE, V, HINT>(src, dst, cv, lane, x0, y, snap, pr,
                                                    [step]() { return step + 1; }, a0, a1, a2);
             }
@@ -208,7 +219,9 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) k_batch(const BatchArgs a
                     p[2] = p2;
                 }
             }
+            item = __shfl_sync(kFull, next, 0) - ticket0;
         }
+        ticket0 += (unsigned)n_items + nwarps;
         if (a.absent_block == (int)blockIdx.x && s == 0) return;  // test hook: never arrives
         if (!grid_barrier(st, a.spin_limit)) return;
         if constexpr (!REDUCE) continue;
@@ -267,7 +280,10 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) k_batch(const BatchArgs a
         }
         if (!grid_barrier(st, a.spin_limit)) return;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->step = step0 + a.nsteps;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {  // every ticket of this launch was drawn before its last barrier
+        st->step = step0 + a.nsteps;
+        st->claim = 0u;
+    }
 }
 
 template <typename S, bool SHIFTED, int HINT, int MINB>
@@ -567,8 +583,10 @@ struct lbm_batch {
             // interrupted launch are partly advanced and must not be trusted
             h_state->err = 0;
             h_state->bar_count = 0;
+            h_state->claim = 0;
             cudaMemcpyAsync(&d_state->err, &h_state->err, sizeof(int), cudaMemcpyHostToDevice, stream);
             cudaMemcpyAsync(&d_state->bar_count, &h_state->bar_count, sizeof(unsigned), cudaMemcpyHostToDevice, stream);
+            cudaMemcpyAsync(&d_state->claim, &h_state->claim, sizeof(unsigned), cudaMemcpyHostToDevice, stream);
             sync();
             step = h_state->step;
             return fail(LBM_ETIMEOUT, "a grid barrier wait of the batch kernel ran out");

@@ -544,8 +544,17 @@ __device__ __forceinline__ void block_partials(C a0, C a1, C a2, double* partial
     }
 }
 
+// Resident blocks per SM the register budget is sized for.  binary16 / bfloat16 storage: 32 warps
+// per SM (64 registers, a few spilled to L1).  Left to itself the compiler takes 80 and leaves 24
+// warps, and these kernels wait on memory latency: f16s 163 -> 170 GLUPS at 4096^2 (bf16s 161 ->
+// 168).  0 (no bound) for the rest -- a bound of 1 is not the same as none, it lets the compiler
+// take more registers; LBM_Q16S, bound by its integer code conversions, lost 4 % at 2048^2 under
+// the same cap.
+template <typename S, int BY>
+inline constexpr int kStepMinBlocks = (sizeof(S) == 2 && !kIsQ16<S>) ? 32 / BY : 0;
+
 template <typename S, bool SHIFTED, bool REDUCE, int V, int R, int BY, int HINT>
-__global__ void __launch_bounds__(32 * BY) k_step(const StepArgs a) {
+__global__ void __launch_bounds__(32 * BY, (kStepMinBlocks<S, BY>)) k_step(const StepArgs a) {
     using C = typename St<S>::C;
     const int lane = threadIdx.x;
     const int x0 = (blockIdx.x * 32 + lane) * V;
