@@ -346,9 +346,11 @@ int lbm_batch_set_shape(lbm_batch *b, int shape);
 
 /* Time every tile shape for `steps` (1..10000) plain steps on the batch's current state (probes
  * off), restore the state exactly (a temporary copy of one population pool is allocated: its
- * size in bytes is lbm_info.device_bytes / 2 at most; LBM_ENOMEM if that fails) and keep the
- * fastest.  chosen (host, may be NULL) receives it, ms (host [LBM_BATCH_SHAPES], may be NULL) the
- * trial times in milliseconds.  Synchronising. */
+ * size in bytes is lbm_info.device_bytes / 2 at most; LBM_ENOMEM if that fails) and keep, among
+ * the shapes within 2 % of the fastest trial, the one with the fewest rows per work item (finer
+ * items keep more warps busy once cavities retire; ties by time).  chosen (host, may be NULL)
+ * receives it, ms (host [LBM_BATCH_SHAPES], may be NULL) the trial times in milliseconds.
+ * Synchronising. */
 int lbm_batch_autotune(lbm_batch *b, int steps, int *chosen, float *ms);
 
 /* Current tile shape, its rows per item, the persistent grid's block count and the number of

@@ -190,6 +190,14 @@ def test_autotune_leaves_the_state_unchanged():
     was never tuned (populations and probe series bitwise; residual to rounding)."""
     cases = CASES[:4]
     cap, every = 300, 3
+    rows = []  # rows per work item of each tile shape
+    b = make_batch(cases, "f32s")
+    try:
+        for s in range(B.LBM_BATCH_SHAPES):
+            B.lbm_batch_set_shape(b, s)
+            rows.append(B.lbm_batch_launch_info(b)[1])
+    finally:
+        B.lbm_batch_destroy(b)
     runs = []
     for tune in (False, True):
         b = make_batch(cases, "f32s")
@@ -201,7 +209,9 @@ def test_autotune_leaves_the_state_unchanged():
             if tune:
                 chosen, ms = B.lbm_batch_autotune(b, 20)
                 assert 0 <= chosen < B.LBM_BATCH_SHAPES and (ms > 0).all()
-                assert ms[chosen] == ms.min()
+                # the fewest rows per item among the shapes within 2 % of the fastest trial
+                near = [s for s in range(B.LBM_BATCH_SHAPES) if ms[s] <= np.float32(1.02) * ms.min()]
+                assert chosen in near and rows[chosen] == min(rows[s] for s in near)
                 assert B.lbm_batch_launch_info(b)[0] == chosen
             B.lbm_batch_step(b, 250)
             r, _ = B.lbm_batch_residual(b, len(cases))
