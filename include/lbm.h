@@ -399,11 +399,16 @@ int lbm_net_forward(lbm_net *n, const float *in, int H, int W, float *out);
  * is 0/1; base, target [3][H][W].  *loss (host, may be NULL).  Synchronising. */
 int lbm_net_backward(lbm_net *n, const float *in, const float *base, const float *target,
                      const float *mask, int H, int W, double *loss);
-/* GEMM back end of the convolutions: 1 = tcgen05 (default; 5th-generation tensor cores, TMEM
+/* GEMM back end of the convolutions: 1 = tcgen05 (5th-generation tensor cores, TMEM
  * accumulator) on an explicit im2col matrix; 2 = tcgen05 with the forward and data-gradient
  * products as implicit GEMMs (the im2col rows are gathered inside the kernel,
  * lbm_nn_conv3x3_bf16_tc05; bitwise the same results as 1, a fifth of the DRAM traffic, but
- * slower: its gather is bound by instruction issue); 0 = mma.sync.  With tcgen05, lbm_net_forward
+ * slower: its gather is bound by instruction issue); 3 = tcgen05 with those products as implicit
+ * GEMMs over a channels-last BF16 copy of the input whose A tiles arrive as TMA boxes
+ * (lbm_nn_conv3x3_bf16_tma; the default: the same sums as 1 in another order, equal to FP32
+ * rounding, and a forward + backward pass 14-22 % faster); the weight gradient always runs on the
+ * explicit im2col; 0 =
+ * mma.sync.  Shapes a back end does not take run on 1.  With tcgen05, lbm_net_forward
  * synchronises, and a bounded tensor-core wait that runs out makes forward/backward return
  * LBM_ETIMEOUT. */
 int lbm_net_set_backend(lbm_net *n, int backend);
@@ -459,6 +464,27 @@ int lbm_nn_gemm_bf16_tc05(int M, int N, int K, const void *A, int lda, const voi
 int lbm_nn_conv3x3_bf16_tc05(const float *x1, int c1, const float *x2, int c2, int H, int W, int K,
                              const void *Wt, int N, float *C, int ldc, int op, int trans_c, int *err,
                              void *stream);
+
+/* Weights of lbm_nn_conv3x3_bf16_tc05's layout (Wt [N][ldk] BF16, k = c*9 + ky*3 + kx, c < C) in
+ * the tap-major layout of lbm_nn_conv3x3_bf16_tma: Wtap[n][tap*Cp + c] = Wt[n][c*9 + tap], tap =
+ * ky*3 + kx, zero for C <= c < Cp, Cp = C rounded up to a multiple of 64.  Wtap: DEVICE, N*9*Cp
+ * BF16, 16-byte aligned.  Asynchronous.  Errors: LBM_EINVAL (NULL, C or N < 1, ldk < 9 C),
+ * LBM_ECUDA. */
+int lbm_nn_weights_tap_major(const void *Wt, int ldk, int C, int N, void *Wtap, void *stream);
+
+/* The same 3x3 convolution as lbm_nn_conv3x3_bf16_tc05 with the gather moved off the SM: one
+ * kernel writes the input channels-last in BF16 (xs: DEVICE scratch of H*W*Cp BF16, 16-byte
+ * aligned, Cp = (c1 + c2) rounded up to 64, zero padded; rounding as the explicit im2col), then
+ * the tcgen05 GEMM runs with K ordered tap-major (k = tap*Cp + c) and fetches each 128-pixel x
+ * 64-channel A tile as one 3-D TMA box shifted by the tap's offset (zeros outside the image).
+ * Wtap: DEVICE [N][9*Cp] BF16 from lbm_nn_weights_tap_major.  C, op, trans_c, err as
+ * lbm_nn_gemm_bf16_tc05 with M = H*W.  H*W must be a multiple of 128 and W a multiple or a divisor
+ * of 128.  The products and their BF16 operands are those of the explicit path; only the order
+ * of the FP32 sums differs.  No counterpart in the paper (the warm start's convolutions).
+ * Asynchronous.  Errors: LBM_EINVAL (shapes, NULL, alignment; nothing launched), LBM_ECUDA. */
+int lbm_nn_conv3x3_bf16_tma(const float *x1, int c1, const float *x2, int c2, int H, int W,
+                            const void *Wtap, int N, float *C, int ldc, int op, int trans_c, void *xs,
+                            int *err, void *stream);
 
 /* ------------------------------------------------------------------ checkpoint */
 

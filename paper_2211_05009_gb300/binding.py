@@ -119,6 +119,8 @@ _SIGS = [
     ("lbm_nn_gemm_bf16_tc05", _I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _I, _I, _P, _P]),
     ("lbm_fma_peak", _I, [_I, _I, _DP, _DP]),
     ("lbm_nn_conv3x3_bf16_tc05", _I, [_P, _I, _P, _I, _I, _I, _I, _P, _I, _P, _I, _I, _I, _P, _P]),
+    ("lbm_nn_weights_tap_major", _I, [_P, _I, _I, _I, _P, _P]),
+    ("lbm_nn_conv3x3_bf16_tma", _I, [_P, _I, _P, _I, _I, _I, _P, _I, _P, _I, _I, _I, _P, _P, _P]),
     ("lbm_save", _I, [_P, ctypes.c_char_p]),
     ("lbm_load", _I, [_P, ctypes.c_char_p]),
 ]
@@ -536,6 +538,15 @@ def lbm_nn_gemm_bf16(M, N, K, A, lda, B, ldb, C, ldc, op=0, split_k=1, stream_ha
 def lbm_nn_conv3x3_bf16_tc05(x1, c1, x2, c2, H, W, K, Wt, N, C, ldc, op, err, trans_c=0, stream_handle=None) -> int:
     return library().lbm_nn_conv3x3_bf16_tc05(_tptr(x1), c1, _tptr(x2) if x2 is not None else None, c2, H, W, K,
                                               _tptr(Wt), N, _tptr(C), ldc, op, trans_c, _tptr(err), stream_handle)
+
+
+def lbm_nn_weights_tap_major(Wt, ldk, C, N, Wtap, stream_handle=None) -> int:
+    return library().lbm_nn_weights_tap_major(_tptr(Wt), ldk, C, N, _tptr(Wtap), stream_handle)
+
+
+def lbm_nn_conv3x3_bf16_tma(x1, c1, x2, c2, H, W, Wtap, N, C, ldc, op, xs, err, trans_c=0, stream_handle=None) -> int:
+    return library().lbm_nn_conv3x3_bf16_tma(_tptr(x1), c1, _tptr(x2) if x2 is not None else None, c2, H, W, _tptr(Wtap),
+                                             N, _tptr(C), ldc, op, trans_c, _tptr(xs), _tptr(err), stream_handle)
 
 
 def lbm_nn_gemm_bf16_tc05(M, N, K, A, lda, B, ldb, C, ldc, op, err, trans_c=0, split_k=1, stream_handle=None) -> int:

@@ -345,15 +345,18 @@ struct lbm_net {
     int H = 0, W = 0;
     std::vector<float*> act, gact;  // per tensor
     std::vector<long long> act_size;
-    __nv_bfloat16* col = nullptr;  // im2col scratch
+    __nv_bfloat16* col = nullptr;  // im2col scratch (backend 3: the channels-last BF16 input)
     long long col_elems = 0;
+    __nv_bfloat16* wtap = nullptr;  // backend 3: the current conv's weights, tap-major
     float* dz = nullptr;            // dZ scratch (largest tensor)
     __nv_bfloat16* dzq = nullptr;   // dZ in BF16
     double* parts = nullptr;
     double* d_loss = nullptr;
     double* h_loss = nullptr;
     int* d_err = nullptr;          // set by a tcgen05 GEMM whose bounded wait ran out
-    int backend = 1;               // 0: mma.sync GEMM, 1: im2col + tcgen05 GEMM, 2: tcgen05 implicit conv
+    int backend = 3;  // 0: mma.sync GEMM, 1: im2col + tcgen05 GEMM, 2: tcgen05 implicit conv (gather),
+                      // 3: tcgen05 implicit conv (channels-last input, TMA boxes); the weight gradient
+                      // always takes the explicit k-major im2col
     cudaStream_t stream = nullptr;
     std::string err;
 
@@ -429,9 +432,11 @@ int ensure_buffers(lbm_net* n, int H, int W) {
     n->gact.clear();
     n->act_size.clear();
     cudaFree(n->col);
+    cudaFree(n->wtap);
     cudaFree(n->dz);
     cudaFree(n->dzq);
     n->col = nullptr;
+    n->wtap = nullptr;
     n->dz = nullptr;
     n->dzq = nullptr;
     Graph g = make_graph(n->ch);
@@ -460,13 +465,18 @@ int ensure_buffers(lbm_net* n, int H, int W) {
         conv_list(n->ch, io);
         const int lv[19] = {0, 0, 1, 1, 2, 2, 3, 3, 4, 4, 3, 3, 2, 2, 1, 1, 0, 0, 0};
         for (int i = 0; i < 19; ++i) {
+            const ConvSpec& c = n->convs[i];
             const long long P = (long long)(H >> lv[i]) * (W >> lv[i]);
-            need = std::max(need, P * (long long)std::max(n->convs[i].Kp, n->convs[i].Kp2));
+            need = std::max(need, P * (long long)std::max(c.Kp, c.Kp2));
+            need = std::max(need, P * (long long)std::max(conv_cp(c.ci), conv_cp(c.co)));  // channels-last inputs
         }
     }
+    long long wtap_elems = 0;
+    for (auto& c : n->convs)
+        wtap_elems = std::max(wtap_elems, 9ll * std::max((long long)c.co * conv_cp(c.ci), (long long)c.ci * conv_cp(c.co)));
     n->col_elems = need;
-    if (cudaMalloc(&n->col, need * 2) != cudaSuccess || cudaMalloc(&n->dz, maxt * 4) != cudaSuccess ||
-        cudaMalloc(&n->dzq, maxt * 2) != cudaSuccess) {
+    if (cudaMalloc(&n->col, need * 2) != cudaSuccess || cudaMalloc(&n->wtap, wtap_elems * 2) != cudaSuccess ||
+        cudaMalloc(&n->dz, maxt * 4) != cudaSuccess || cudaMalloc(&n->dzq, maxt * 2) != cudaSuccess) {
         cudaGetLastError();
         return n->fail(LBM_ENOMEM, "network scratch buffers");
     }
@@ -490,12 +500,20 @@ int prep_weights(lbm_net* n) {
 int conv_fwd(lbm_net* n, const ConvSpec& c, const float* x1, int c1, const float* x2, int c2, int H, int W, float* y) {
     const long long P = (long long)H * W;
     int rc = LBM_OK;
-    bool implicit = n->backend == 2;
-    if (implicit) {  // implicit GEMM: the im2col rows are gathered inside the tensor-core kernel
+    bool implicit = n->backend == 2 || n->backend == 3;
+    if (n->backend == 2) {  // implicit GEMM: the im2col rows are gathered inside the tensor-core kernel
         const cudaError_t e = conv3x3_bf16_umma(x1, c1, x2, c2, H, W, c.Kp, n->wq + c.wq_off, c.co, y, (int)P, kStore,
                                                 true, n->d_err, n->stream);
         if (e == cudaErrorInvalidValue) implicit = false;  // shape it does not take: explicit im2col below
         else rc = n->cuda(e, "conv (tcgen05 implicit)");
+    } else if (n->backend == 3) {  // implicit GEMM over the channels-last input, A tiles by TMA boxes
+        rc = n->cuda(weights_tap_major(n->wq + c.wq_off, c.Kp, c1 + c2, c.co, n->wtap, n->stream), "tap-major weights");
+        if (!rc) {
+            const cudaError_t e = conv3x3_bf16_tma(x1, c1, x2, c2, H, W, n->wtap, c.co, y, (int)P, kStore, true, n->col,
+                                                   n->d_err, n->stream);
+            if (e == cudaErrorInvalidValue) implicit = false;  // shape it does not take: explicit im2col below
+            else rc = n->cuda(e, "conv (tcgen05, TMA boxes)");
+        }
     }
     if (!implicit) {
         k_im2col_pk<<<nblk(P * c.Kp), 256, 0, n->stream>>>(x1, c1, x2, c2, H, W, c.Kp, n->col);
@@ -542,8 +560,23 @@ int conv_bwd(lbm_net* n, const ConvSpec& c, const float* x1, int c1, const float
     if (!rc && (gx1 || gx2)) {
         const __nv_bfloat16* wf1 = n->wf + c.wf_off;
         const __nv_bfloat16* wf2 = wf1 + (long long)c1 * c.Kp2;
-        bool implicit = n->backend == 2;
-        if (implicit) {  // implicit GEMM over dZ (co channels) with the flipped weights
+        bool implicit = n->backend == 2 || n->backend == 3;
+        if (n->backend == 3) {  // over dZ (co channels) with the flipped weights, tap-major
+            bool first = true;
+            for (int part = 0; part < 2 && !rc && implicit; ++part) {
+                float* gx = part == 0 ? gx1 : gx2;
+                if (!gx) continue;
+                const int rows = part == 0 ? c1 : c2;
+                rc = n->cuda(weights_tap_major(part == 0 ? wf1 : wf2, c.Kp2, c.co, rows, n->wtap, n->stream),
+                             "tap-major weights");
+                if (rc) break;
+                const cudaError_t e = conv3x3_bf16_tma(n->dz, c.co, nullptr, 0, H, W, n->wtap, rows, gx, (int)P, kAccumulate,
+                                                       true, n->col, n->d_err, n->stream);
+                if (e == cudaErrorInvalidValue && first) implicit = false;  // explicit im2col below
+                else rc = n->cuda(e, "data-gradient conv (tcgen05, TMA boxes)");
+                first = false;
+            }
+        } else if (implicit) {  // implicit GEMM over dZ (co channels) with the flipped weights
             bool first = true;  // a shape the kernel does not take is refused before anything launches
             for (int part = 0; part < 2 && !rc && implicit; ++part) {
                 float* gx = part == 0 ? gx1 : gx2;
@@ -720,7 +753,8 @@ extern "C" void lbm_net_destroy(lbm_net* n) {
     for (float* p : n->act) cudaFree(p);
     for (float* p : n->gact) cudaFree(p);
     for (void* p : {(void*)n->params, (void*)n->grads, (void*)n->adam_m, (void*)n->adam_v, (void*)n->wq, (void*)n->wf,
-                    (void*)n->col, (void*)n->dz, (void*)n->dzq, (void*)n->parts, (void*)n->d_loss, (void*)n->d_err})
+                    (void*)n->col, (void*)n->wtap, (void*)n->dz, (void*)n->dzq, (void*)n->parts, (void*)n->d_loss,
+                    (void*)n->d_err})
         if (p) cudaFree(p);
     if (n->h_loss) cudaFreeHost(n->h_loss);
     delete n;
@@ -766,7 +800,7 @@ static int check_err(lbm_net* n) {
 }
 
 extern "C" int lbm_net_set_backend(lbm_net* n, int backend) {
-    if (!n || backend < 0 || backend > 2) return LBM_EINVAL;
+    if (!n || backend < 0 || backend > 3) return LBM_EINVAL;
     n->backend = backend;
     return LBM_OK;
 }
@@ -908,6 +942,24 @@ extern "C" int lbm_nn_conv3x3_bf16_tc05(const float* x1, int c1, const float* x2
     if (!x1 || !Wt || !C || !err || op < 0 || op > 2 || H < 1 || W < 1) return LBM_EINVAL;
     const cudaError_t e = conv3x3_bf16_umma(x1, c1, x2, c2, H, W, K, static_cast<const __nv_bfloat16*>(Wt), N, C, ldc,
                                             (GemmOp)op, trans_c != 0, err, (cudaStream_t)stream);
+    if (e == cudaErrorInvalidValue) return LBM_EINVAL;
+    return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
+
+extern "C" int lbm_nn_weights_tap_major(const void* Wt, int ldk, int C, int N, void* Wtap, void* stream) {
+    if (!Wt || !Wtap || C < 1 || N < 1 || ldk < 9 * C) return LBM_EINVAL;
+    const cudaError_t e = weights_tap_major(static_cast<const __nv_bfloat16*>(Wt), ldk, C, N,
+                                            static_cast<__nv_bfloat16*>(Wtap), (cudaStream_t)stream);
+    if (e == cudaErrorInvalidValue) return LBM_EINVAL;
+    return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
+
+extern "C" int lbm_nn_conv3x3_bf16_tma(const float* x1, int c1, const float* x2, int c2, int H, int W, const void* Wtap,
+                                       int N, float* C, int ldc, int op, int trans_c, void* xs, int* err, void* stream) {
+    if (!x1 || !Wtap || !C || !xs || !err || op < 0 || op > 2 || H < 1 || W < 1) return LBM_EINVAL;
+    const cudaError_t e = conv3x3_bf16_tma(x1, c1, x2, c2, H, W, static_cast<const __nv_bfloat16*>(Wtap), N, C, ldc,
+                                           (GemmOp)op, trans_c != 0, static_cast<__nv_bfloat16*>(xs), err,
+                                           (cudaStream_t)stream);
     if (e == cudaErrorInvalidValue) return LBM_EINVAL;
     return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }

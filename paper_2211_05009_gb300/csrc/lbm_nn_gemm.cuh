@@ -39,5 +39,17 @@ cudaError_t conv3x3_bf16_umma(const float* x1, int c1, const float* x2, int c2, 
                               const __nv_bfloat16* Wt, int N, float* C, int ldc, GemmOp op, bool trans_c, int* err,
                               cudaStream_t st);
 
+// The same convolution with the input stored channels-last in BF16 and K ordered tap-major, so
+// that each 128 x 64 A tile is one 3-D TMA box (no gather on the SM).  Cp = conv_cp(c1 + c2) (the
+// channels rounded up to 64, zero padded).  xs: scratch of H*W*Cp BF16 that receives the
+// channels-last input; Wtap: [N][9 * Cp] BF16 from weights_tap_major.  H*W a multiple of 128 and
+// W a multiple or a divisor of 128, else cudaErrorInvalidValue (nothing launched).  The sums are
+// those of the explicit path in another order, so results agree to FP32 rounding, not bitwise.
+int conv_cp(int c);
+cudaError_t weights_tap_major(const __nv_bfloat16* Wt, int ldk, int C, int N, __nv_bfloat16* Wtap, cudaStream_t st);
+cudaError_t conv3x3_bf16_tma(const float* x1, int c1, const float* x2, int c2, int H, int W, const __nv_bfloat16* Wtap,
+                             int N, float* C, int ldc, GemmOp op, bool trans_c, __nv_bfloat16* xs, int* err,
+                             cudaStream_t st);
+
 }  // namespace nn
 }  // namespace lbm

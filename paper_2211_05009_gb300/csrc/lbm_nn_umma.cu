@@ -95,10 +95,30 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+// Geometry of the convolution form (CONV = true): image width W, 64-channel blocks per tap cb.
+struct ConvGeo {
+    int W, cb;
+};
+
+// CONV = false: the GEMM above.  CONV = true: A is a 3x3, padding-1 convolution input stored
+// channels-last in BF16 ([H][W][Cp], Cp = cb * 64) and K is ordered tap-major (k = tap * Cp + c,
+// tap = ky * 3 + kx).  The 128 pixels of an M tile are 128 consecutive pixels of one row (W a
+// multiple of 128) or 128 / W whole rows (W dividing 128), so the A tile of K step t -- tap
+// t / cb, channels (t % cb) * 64 .. +63 -- is one 3-D TMA box of that shape shifted by
+// (kx - 1, ky - 1) pixels: the TMA fills the image border with zeros, and the stage lands in
+// shared memory exactly as the GEMM's 128 x 64 A tile does.  No gather runs on the SM.
+template <bool CONV>
 __global__ void __launch_bounds__(128, 1)
     k_gemm_tc05(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
                 float* __restrict__ C, int ldc, int op, int trans_c, int k_per_split, int tn, int cols, int stages,
-                int* err) {
+                int* err, ConvGeo geo) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int stage_bytes = kTileA + tn * TK * 2;
@@ -147,7 +167,14 @@ __global__ void __launch_bounds__(128, 1)
             }
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(sa(&full[s])), "r"(stage_bytes)
                          : "memory");
-            tma_load_2d(sA(s), &tmA, kb + t * TK, m0, sa(&full[s]));
+            if constexpr (CONV) {
+                const int tap = t / geo.cb;
+                const int c0 = (t - tap * geo.cb) * TK;
+                const int x = (geo.W > TM ? m0 % geo.W : 0) + tap % 3 - 1;
+                tma_load_3d(sA(s), &tmA, c0, x, m0 / geo.W + tap / 3 - 1, sa(&full[s]));
+            } else {
+                tma_load_2d(sA(s), &tmA, kb + t * TK, m0, sa(&full[s]));
+            }
             tma_load_2d(sB(s), &tmB, kb + t * TK, n0, sa(&full[s]));
         }
         if (abort_flag)  // the copies already issued must land before the CTA may leave
@@ -488,6 +515,51 @@ bool make_map(CUtensorMap* m, const __nv_bfloat16* X, int rows, int K, int ld, i
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Channels-last activation [H][W][Cp] bfloat16 as a 3-D tensor {Cp, W, H}, box {64, bw, bh} with
+// bw * bh = 128 pixels, 128-byte swizzle, zero fill out of range (the convolution's border).
+bool make_act_map(CUtensorMap* m, const __nv_bfloat16* X, int H, int W, int Cp, int bw, int bh) {
+    auto enc = encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)Cp, (cuuint64_t)W, (cuuint64_t)H};
+    const cuuint64_t strides[2] = {(cuuint64_t)Cp * 2, (cuuint64_t)W * Cp * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)TK, (cuuint32_t)bw, (cuuint32_t)bh};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(X), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// X[p][c] = bf16(x1 ++ x2 channel c at pixel p), zero for c >= c1 + c2: one pixel and 8 channels per
+// thread (reads coalesced along the pixels, one 16-byte store), rounding as the explicit im2col.
+__global__ void k_channels_last_bf16(const float* __restrict__ x1, int c1, const float* __restrict__ x2, int c2,
+                                     long long P, int Cp, __nv_bfloat16* __restrict__ X) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int cg = blockIdx.y * 8;
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int c = cg + j;
+        v[j] = c < c1 ? x1[(long long)c * P + p] : (c < c1 + c2 ? x2[(long long)(c - c1) * P + p] : 0.f);
+    }
+    uint4 w;
+    w.x = bf16x2(v[0], v[1]);
+    w.y = bf16x2(v[2], v[3]);
+    w.z = bf16x2(v[4], v[5]);
+    w.w = bf16x2(v[6], v[7]);
+    *reinterpret_cast<uint4*>(X + p * Cp + cg) = w;
+}
+
+// Wtap[n][tap * Cp + c] = Wt[n][c * 9 + tap] for c < C, zero for C <= c < Cp.
+__global__ void k_weights_tap_major(const __nv_bfloat16* __restrict__ Wt, int ldk, int C, int N, int Cp,
+                                    __nv_bfloat16* __restrict__ Wtap) {
+    const long long per = 9ll * Cp;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= per * N) return;
+    const int n = (int)(i / per), r = (int)(i - n * per), tap = r / Cp, c = r - tap * Cp;
+    Wtap[i] = c < C ? Wt[(long long)n * ldk + c * 9 + tap] : __float2bfloat16_rn(0.f);
+}
+
 }  // namespace
 
 cudaError_t gemm_bf16_nt_umma(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
@@ -510,7 +582,7 @@ cudaError_t gemm_bf16_nt_umma(int M, int N, int K, const __nv_bfloat16* A, int l
         if (e != cudaSuccess) return e;
         std::lock_guard<std::mutex> lock(mu);
         if (dev >= 64 || p.smem > opted[dev]) {
-            e = cudaFuncSetAttribute(k_gemm_tc05, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
+            e = cudaFuncSetAttribute(k_gemm_tc05<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
             if (e != cudaSuccess) return e;
             if (dev < 64) opted[dev] = p.smem;
         }
@@ -519,8 +591,8 @@ cudaError_t gemm_bf16_nt_umma(int M, int N, int K, const __nv_bfloat16* A, int l
     kps = (kps + TK - 1) / TK * TK;
     split_k = (K + kps - 1) / kps;
     const dim3 grid(p.tiles_n, (M + TM - 1) / TM, split_k);
-    k_gemm_tc05<<<grid, 128, p.smem, st>>>(ma, mb, M, N, K, C, ldc, (int)op, trans_c ? 1 : 0, kps, p.tn, p.cols,
-                                            p.stages, err);
+    k_gemm_tc05<false><<<grid, 128, p.smem, st>>>(ma, mb, M, N, K, C, ldc, (int)op, trans_c ? 1 : 0, kps, p.tn, p.cols,
+                                                   p.stages, err, ConvGeo{0, 0});
     return cudaGetLastError();
 }
 
@@ -566,6 +638,58 @@ cudaError_t conv3x3_bf16_umma(const float* x1, int c1, const float* x2, int c2, 
     const ConvIn in{x1, x2, c1, c2, H, W, win};
     const dim3 grid(1, (unsigned)((P + TM - 1) / TM), 1);
     k_conv_tc05<<<grid, kConvThreads, p.smem, st>>>(in, mb, N, K, C, ldc, (int)op, trans_c ? 1 : 0, p.tn, p.cols, p.stages, err);
+    return cudaGetLastError();
+}
+
+}  // namespace nn
+}  // namespace lbm
+
+namespace lbm {
+namespace nn {
+
+int conv_cp(int c) { return (c + TK - 1) / TK * TK; }
+
+cudaError_t weights_tap_major(const __nv_bfloat16* Wt, int ldk, int C, int N, __nv_bfloat16* Wtap, cudaStream_t st) {
+    if (N <= 0 || C <= 0) return cudaSuccess;
+    if (!Wt || !Wtap || ldk < 9 * C) return cudaErrorInvalidValue;
+    const long long total = 9ll * conv_cp(C) * N;
+    k_weights_tap_major<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(Wt, ldk, C, N, conv_cp(C), Wtap);
+    return cudaGetLastError();
+}
+
+cudaError_t conv3x3_bf16_tma(const float* x1, int c1, const float* x2, int c2, int H, int W, const __nv_bfloat16* Wtap,
+                             int N, float* C, int ldc, GemmOp op, bool trans_c, __nv_bfloat16* xs, int* err,
+                             cudaStream_t st) {
+    const long long P = (long long)H * W;
+    if (P <= 0 || N <= 0) return cudaSuccess;
+    if (!x1 || c1 < 1 || c2 < 0 || (c2 > 0 && !x2) || !Wtap || !xs || !err) return cudaErrorInvalidValue;
+    // tiles of 128 pixels: part of one row, or whole rows; the box's dimensions stay <= 256
+    if (P % TM || !(W % TM == 0 || TM % W == 0) || H > 0x7fffffff / W) return cudaErrorInvalidValue;
+    if (((uintptr_t)Wtap & 15) || ((uintptr_t)xs & 15)) return cudaErrorInvalidValue;
+    const int Cp = conv_cp(c1 + c2), K = 9 * Cp;
+    const Plan p = plan_for(N);
+    CUtensorMap ma, mb;
+    const int bw = W < TM ? W : TM;
+    if (!make_act_map(&ma, xs, H, W, Cp, bw, TM / bw) || !make_map(&mb, Wtap, N, K, K, p.tn)) return cudaErrorInvalidValue;
+    {
+        static std::mutex mu;
+        static int opted[64] = {};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        std::lock_guard<std::mutex> lock(mu);
+        if (dev >= 64 || p.smem > opted[dev]) {
+            e = cudaFuncSetAttribute(k_gemm_tc05<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
+            if (e != cudaSuccess) return e;
+            if (dev < 64) opted[dev] = p.smem;
+        }
+    }
+    k_channels_last_bf16<<<dim3((unsigned)((P + 255) / 256), (unsigned)(Cp / 8)), 256, 0, st>>>(x1, c1, x2, c2, P, Cp, xs);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const dim3 grid(p.tiles_n, (unsigned)(P / TM), 1);
+    k_gemm_tc05<true><<<grid, 128, p.smem, st>>>(ma, mb, (int)P, N, K, C, ldc, (int)op, trans_c ? 1 : 0, K, p.tn, p.cols,
+                                                  p.stages, err, ConvGeo{W, Cp / TK});
     return cudaGetLastError();
 }
 

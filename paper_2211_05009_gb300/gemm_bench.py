@@ -26,8 +26,9 @@ def main(argv=None):
     ap.add_argument("--cin", type=int, default=160)
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--conv", type=int, default=0, metavar="SIDE",
-                    help="instead: the implicit-GEMM convolution on a SIDE x SIDE image against the same "
-                         "tcgen05 GEMM on its explicit im2col (built here with torch, not timed)")
+                    help="instead: the implicit-GEMM convolutions (gathered, and by TMA boxes over a channels-last "
+                         "copy) on a SIDE x SIDE image against the same tcgen05 GEMM on its explicit im2col "
+                         "(built here with torch, not timed)")
     a = ap.parse_args(argv)
     build()
     if a.conv:
@@ -76,8 +77,16 @@ def conv_main(a):
     A[:, :C * 9] = cols.t().to(torch.bfloat16)
     Y1 = torch.empty(N, P, dtype=torch.float32, device="cuda")
     Y2 = torch.empty(N, P, dtype=torch.float32, device="cuda")
+    Y3 = torch.empty(N, P, dtype=torch.float32, device="cuda")
+    Cp = (C + 63) // 64 * 64
+    Wtap = torch.empty(N, 9 * Cp, dtype=torch.bfloat16, device="cuda")
+    xs = torch.empty(P * Cp, dtype=torch.bfloat16, device="cuda")
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
     st = torch.cuda.current_stream()
+    assert B.lbm_nn_weights_tap_major(Wt, K, C, N, Wtap, st.cuda_stream) == B.LBM_OK
+
+    def tma():
+        assert B.lbm_nn_conv3x3_bf16_tma(x, C, None, 0, H, W, Wtap, N, Y3, P, 0, xs, err, 1, st.cuda_stream) == B.LBM_OK
 
     def implicit():
         assert B.lbm_nn_conv3x3_bf16_tc05(x, C, None, 0, H, W, K, Wt, N, Y1, P, 0, err, 1, st.cuda_stream) == B.LBM_OK
@@ -86,7 +95,7 @@ def conv_main(a):
         assert B.lbm_nn_gemm_bf16_tc05(P, N, K, A, K, Wt, K, Y2, P, 0, err, 1, 1, st.cuda_stream) == B.LBM_OK
 
     out = {"H": H, "W": W, "M": P, "N": N, "K": K}
-    for name, fn in (("implicit_conv", implicit), ("gemm_on_explicit_im2col", explicit)):
+    for name, fn in (("tma_conv", tma), ("implicit_conv", implicit), ("gemm_on_explicit_im2col", explicit)):
         fn()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -98,6 +107,14 @@ def conv_main(a):
         sec = e0.elapsed_time(e1) / 1e3 / a.reps
         out[name] = {"us": sec * 1e6, "tflops": 2.0 * P * N * K / sec / 1e12}
     out["bitwise_equal"] = bool(torch.equal(Y1, Y2))
+    # the TMA form sums the same BF16 products in another order: compare with FP64 on every 16th pixel
+    rows = torch.arange(0, P, 16, device="cuda")
+    As, Ws = A[rows, :C * 9].double(), Wt[:, :C * 9].double()
+    ref, scale = (As @ Ws.t()).t(), (As.abs() @ Ws.abs().t()).t()
+    out["tma_max_err_over_abs_sum"] = float(((Y3[:, rows].double() - ref).abs() / scale.clamp_min(1e-30)).max())
+    out["explicit_max_err_over_abs_sum"] = float(((Y2[:, rows].double() - ref).abs() / scale.clamp_min(1e-30)).max())
+    out["tma_conv"]["tflops_issued"] = out["tma_conv"]["tflops"] * (9 * Cp) / K
+    out["bytes_tma_algorithmic"] = C * P * 4 + P * Cp * 2 + N * 9 * Cp * 2 + N * P * 4
     out["tcgen05_wait_error"] = int(err.item())
     out["bytes_implicit_algorithmic"] = C * P * 4 + N * K * 2 + N * P * 4
     out["bytes_explicit_algorithmic"] = P * K * 2 + N * K * 2 + N * P * 4

@@ -83,7 +83,7 @@ def _setup(width=4, H=64, W=64, seed=7, backend=1):
     return n, params32, arrs, dev
 
 
-@pytest.mark.parametrize("backend", [1, 0])
+@pytest.mark.parametrize("backend", [1, 0, 3])
 def test_network_forward_matches_oracle(backend):
     H = W = 64
     n, p, (x, base, tgt, mask), (dx, dbase, dtgt, dmask) = _setup(H=H, W=W, backend=backend)
@@ -100,7 +100,7 @@ def test_network_forward_matches_oracle(backend):
         B.lbm_net_destroy(n)
 
 
-@pytest.mark.parametrize("backend", [1, 0])
+@pytest.mark.parametrize("backend", [1, 0, 3])
 def test_network_loss_and_gradients_match_oracle(backend):
     H = W = 64
     n, p, (x, base, tgt, mask), (dx, dbase, dtgt, dmask) = _setup(H=H, W=W, backend=backend)
@@ -275,6 +275,63 @@ def test_implicit_conv_equals_explicit_im2col_gemm(c1, c2, H, W, N):
     assert torch.equal(out, ref_c)
     ref = (A.double().numpy() @ Wt.double().numpy().T).T
     assert np.abs(out.cpu().numpy() - ref).max() / np.abs(ref).max() < 1e-5
+
+
+@pytest.mark.parametrize("c1,c2,H,W,N,op,trans", [(3, 0, 2, 256, 20, 0, 1), (7, 5, 16, 128, 40, 0, 1),
+                                                  (40, 20, 8, 64, 160, 0, 1), (70, 0, 32, 16, 72, 0, 1),
+                                                  (100, 60, 64, 8, 256, 0, 1), (5, 0, 16, 32, 24, 1, 0)])
+def test_tma_conv_matches_fp64_of_bf16_inputs(c1, c2, H, W, N, op, trans):
+    """lbm_nn_conv3x3_bf16_tma: the tap-major weights are the permutation of their definition, and
+    the convolution equals the FP64 product of the BF16-rounded explicit im2col and weights to FP32
+    summation rounding (1e-5 of the sum of absolute products).  Covers one-row boxes (W >= 128),
+    several-row boxes (W < 128), channel padding to 64, two 64-channel blocks per tap, N = 256, and
+    the accumulate / row-major epilogue."""
+    g = torch.Generator(device="cpu").manual_seed(c1 * 1000 + W)
+    C, P = c1 + c2, H * W
+    K = (C * 9 + 7) // 8 * 8
+    Cp = (C + 63) // 64 * 64
+    x = torch.randn(C, H, W, generator=g)
+    Wt = torch.randn(N, K, generator=g).to(torch.bfloat16)
+    Wt[:, C * 9:] = 0
+    x1 = x[:c1].contiguous().cuda()
+    x2 = x[c1:].contiguous().cuda() if c2 else None
+    Wtap = torch.full((N, 9 * Cp), float("nan"), dtype=torch.bfloat16, device="cuda")
+    assert B.lbm_nn_weights_tap_major(Wt.cuda(), K, C, N, Wtap) == B.LBM_OK
+    want = torch.zeros(N, 9, Cp, dtype=torch.bfloat16)
+    want[:, :, :C] = Wt[:, :C * 9].reshape(N, C, 9).transpose(1, 2)
+    torch.cuda.synchronize()
+    assert torch.equal(Wtap.cpu(), want.reshape(N, 9 * Cp))
+    xs = torch.empty(P * Cp, dtype=torch.bfloat16, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    init = torch.randn((N, P) if trans else (P, N), generator=g)
+    out = init.clone().cuda()
+    ldc = P if trans else N
+    assert B.lbm_nn_conv3x3_bf16_tma(x1, c1, x2, c2, H, W, Wtap, N, out, ldc, op, xs, err, trans_c=trans) == B.LBM_OK
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    A = torch.tensor(_im2col_pk(x.double().numpy(), H, W, K)).to(torch.bfloat16).double().numpy()[:, :C * 9]
+    Wd = Wt[:, :C * 9].double().numpy()
+    ref, scale = A @ Wd.T, np.abs(A) @ np.abs(Wd).T  # [P][N]
+    if op == 1:
+        ref = ref + (init.double().numpy().T if trans else init.double().numpy())
+    got = out.double().cpu().numpy()
+    got = got.T if trans else got
+    assert np.all(np.isfinite(got))
+    assert (np.abs(got - ref) / np.maximum(scale, 1e-30)).max() < 1e-5
+
+
+def test_tma_conv_refuses_shapes_it_does_not_take():
+    """W neither a multiple nor a divisor of 128, or H*W not a multiple of 128: LBM_EINVAL and
+    nothing written."""
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for H, W in ((16, 40), (3, 64), (1, 96)):
+        x = torch.randn(4, H, W, device="cuda")
+        Wtap = torch.zeros(16, 9 * 64, dtype=torch.bfloat16, device="cuda")
+        xs = torch.full((H * W * 64,), 7.0, dtype=torch.bfloat16, device="cuda")
+        out = torch.full((16, H * W), float("nan"), device="cuda")
+        assert B.lbm_nn_conv3x3_bf16_tma(x, 4, None, 0, H, W, Wtap, 16, out, H * W, 0, xs, err, trans_c=1) == B.LBM_EINVAL
+        torch.cuda.synchronize()
+        assert torch.isnan(out).all() and (xs == 7.0).all()
 
 
 def test_network_implicit_and_explicit_backends_agree():
