@@ -335,13 +335,15 @@ int lbm_batch_probe(lbm_batch *b, const double *x, const double *y, int every, d
 int lbm_batch_info(lbm_batch *b, int i, lbm_info *info);
 
 /* Tile shapes of the batch kernel (no counterpart in the paper): rows per work item x load path x
- * resident 128-thread blocks per SM (register budget 96 for 5, 128 for 4)
+ * resident 128-thread blocks per SM (register budget 96 for 5, 128 for 4, 64 for 8)
  *   0: 2 rows, L2 loads, 5 (default)  1: 1 row, L2, 5         2: 4 rows, L2, 5
  *   3: 2 rows, L1-cached loads, 5     4: 1 row, L1, 5         5: 4 rows, L1, 5
- *   6: 2 rows, L1, 4                  7: 4 rows, L1, 4
+ *   6: 2 rows, L1, 4                  7: 4 rows, L1, 4        8: 2 rows, L2, 8
+ *   9: 4 rows, L1, 8
  * Every shape computes bitwise-identical populations; Eq. 6 partial sums group per item, so
- * residuals agree to rounding.  lbm_batch_set_shape synchronises; LBM_EINVAL outside 0..7. */
-#define LBM_BATCH_SHAPES 8
+ * residuals agree to rounding.  lbm_batch_set_shape synchronises; LBM_EINVAL outside
+ * 0..LBM_BATCH_SHAPES-1. */
+#define LBM_BATCH_SHAPES 10
 int lbm_batch_set_shape(lbm_batch *b, int shape);
 
 /* Time every tile shape for `steps` (1..10000) plain steps on the batch's current state (probes

@@ -23,7 +23,7 @@ LBM_STATIC_SCRATCH_DOUBLES = 1 << 19
 DTYPES = {"f64": 0, "f32": 1, "f32s": 2, "f16s": 3, "bf16s": 4, "q16s": 5}
 LBM_FLAG_LID_CORNERS_MOVING = 1
 LBM_MAX_PROBES = 4
-LBM_BATCH_SHAPES = 8
+LBM_BATCH_SHAPES = 10
 LBM_INIT_NEQ = 1
 LBM_BATCH_MAX = 512
 RESIDUAL_INTERVAL = 100

@@ -40,12 +40,15 @@ constexpr int kBatchThreads = 128;
 static_assert((kBatchThreads & (kBatchThreads - 1)) == 0, "tree reductions assume a power of two");
 
 // Tile shapes: rows per work item x load hint (2: ld.global.cg, 3: ld.global.ca) x resident
-// blocks per SM the register budget is sized for (5: 96 registers, 4: 128).
+// blocks per SM the register budget is sized for (5: 96 registers, 4: 128, 8: 64).  The 8-block
+// shapes are for 16-bit storage, whose kernels fit 64 registers without spilling and wait on
+// memory latency (45-cavity batch, f16s 124.8 -> 136.5 GLUPS); FP32 spills there and FP64 wants
+// the 4-block budget, and the autotuner keeps whichever is fastest.
 struct BatchShape {
     int rows, hint, minb;
 };
-constexpr BatchShape kBatchShapes[LBM_BATCH_SHAPES] = {{2, 2, 5}, {1, 2, 5}, {4, 2, 5}, {2, 3, 5},
-                                                       {1, 3, 5}, {4, 3, 5}, {2, 3, 4}, {4, 3, 4}};
+constexpr BatchShape kBatchShapes[LBM_BATCH_SHAPES] = {{2, 2, 5}, {1, 2, 5}, {4, 2, 5}, {2, 3, 5}, {1, 3, 5},
+                                                       {4, 3, 5}, {2, 3, 4}, {4, 3, 4}, {2, 2, 8}, {4, 3, 8}};
 
 struct BatchCav {
     long long off;       // population offset (storage elements) in each pool
@@ -307,6 +310,8 @@ static cudaError_t launch_batch_t(const BatchShape& sh, const BatchArgs& a, bool
     if (sh.hint == 2 && sh.minb == 5) return launch_batch_h<S, SHIFTED, 2, 5>(a, reduce, blocks, st);
     if (sh.hint == 3 && sh.minb == 5) return launch_batch_h<S, SHIFTED, 3, 5>(a, reduce, blocks, st);
     if (sh.hint == 3 && sh.minb == 4) return launch_batch_h<S, SHIFTED, 3, 4>(a, reduce, blocks, st);
+    if (sh.hint == 2 && sh.minb == 8) return launch_batch_h<S, SHIFTED, 2, 8>(a, reduce, blocks, st);
+    if (sh.hint == 3 && sh.minb == 8) return launch_batch_h<S, SHIFTED, 3, 8>(a, reduce, blocks, st);
     return cudaErrorInvalidValue;
 }
 
@@ -326,6 +331,8 @@ static int batch_blocks_t(const BatchShape& sh) {
     if (sh.hint == 2 && sh.minb == 5) return batch_blocks_h<S, SHIFTED, 2, 5>();
     if (sh.hint == 3 && sh.minb == 5) return batch_blocks_h<S, SHIFTED, 3, 5>();
     if (sh.hint == 3 && sh.minb == 4) return batch_blocks_h<S, SHIFTED, 3, 4>();
+    if (sh.hint == 2 && sh.minb == 8) return batch_blocks_h<S, SHIFTED, 2, 8>();
+    if (sh.hint == 3 && sh.minb == 8) return batch_blocks_h<S, SHIFTED, 3, 8>();
     return 0;
 }
 
