@@ -611,8 +611,15 @@ extern "C" int lbm_set_moments_ex(lbm_ctx* c, const double* rho, const double* u
     }
     if (rc) return rc;
     c->step = 0;
-    for (int q = 0; q < c->probes.n; ++q) c->probes.start[q] = 0;
-    c->invalidate_graphs();
+    // the captured 100-step graphs hold the probe set by value and nothing else that this call
+    // changes (the step counter picks a graph, the state lives in device memory): keep them unless
+    // a probe's start step moves, so that re-seeding the field every 100 steps costs no capture
+    bool probes_moved = false;
+    for (int q = 0; q < c->probes.n; ++q) {
+        probes_moved |= c->probes.start[q] != 0;
+        c->probes.start[q] = 0;
+    }
+    if (probes_moved) c->invalidate_graphs();
     // the state reset comes first: the LBM_Q16S populations are stored against its reference density
     rc = c->cuda(cudaMemsetAsync(c->d_state, 0, sizeof(DevState), c->stream), "state reset");
     if (!rc)

@@ -172,6 +172,44 @@ def test_set_moments_gives_equilibrium():
     assert np.abs(f - ref).max() < 1e-16 * 8
 
 
+def test_set_moments_keeps_graphs_and_matches_a_fresh_context():
+    """Re-seeding a running context (whose 100-step graphs exist) with lbm_set_moments gives, over
+    the next 200 steps, bitwise the populations, Eq. 6 residual and probe series of a fresh context
+    seeded the same way: the graphs it keeps (no probe moved) are the ones a fresh context builds."""
+    nx, ny, Re, U = 96, 70, 400.0, 0.1
+    st = torch.cuda.current_stream().cuda_stream
+    cap, every = 200, 2
+    out = []
+    for fresh in (False, True):
+        ctx = B.lbm_create(nx, ny, Re, U, "f32s")
+        try:
+            B.lbm_set_stream(ctx, st)
+            series = torch.full((cap, 2), float("nan"), dtype=torch.float64, device="cuda")
+            B.lbm_probe(ctx, 0.5, 0.4, every, series, cap)
+            seed = [torch.empty((ny, nx), dtype=torch.float64, device="cuda") for _ in range(3)]
+            if fresh:
+                seed_ctx = B.lbm_create(nx, ny, Re, U, "f32s")
+                B.lbm_set_stream(seed_ctx, st)
+                B.lbm_step(seed_ctx, 300)
+                B.lbm_moments(seed_ctx, *seed)
+                B.lbm_destroy(seed_ctx)
+            else:
+                B.lbm_step(ctx, 300)  # builds and replays the graphs
+                B.lbm_moments(ctx, *seed)
+            B.lbm_set_moments(ctx, *seed)
+            B.lbm_step(ctx, 200)
+            r = B.lbm_residual(ctx)
+            f = torch.empty((9, ny, nx), dtype=torch.float64, device="cuda")
+            B.lbm_get_populations(ctx, f)
+            torch.cuda.synchronize()
+            out.append((f.cpu(), r, series[:200 // every].cpu()))
+        finally:
+            B.lbm_destroy(ctx)
+    (f0, r0, s0), (f1, r1, s1) = out
+    assert torch.equal(f0, f1) and r0 == r1 and torch.equal(s0, s1)
+    assert torch.isfinite(s0).all()
+
+
 @pytest.mark.parametrize("dtype,tol", [("f64", 1e-13), ("f32s", 3e-7), ("f32", 3e-7), ("f16s", 2e-3)])
 def test_set_moments_neq_matches_oracle(dtype, tol):
     """LBM_INIT_NEQ: f^eq plus (1 - 1/tau) times the first-order Chapman-Enskog part, on
