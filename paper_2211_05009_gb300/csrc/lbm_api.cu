@@ -217,6 +217,17 @@ struct lbm_ctx {
         if (stage_bytes < offset + bytes) return nullptr;
         return (double*)((char*)stage + offset);
     }
+    // Device address of page-locked host memory mapped into the device's address space (pinned
+    // allocations under unified addressing), or null: such buffers are read or written by the
+    // kernels directly over the host link instead of through the staging buffer and a copy.
+    static double* mapped_host(const void* p) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return at.type == cudaMemoryTypeHost ? static_cast<double*>(at.devicePointer) : nullptr;
+    }
     int ensure_stage(size_t bytes) {
         if (stage_bytes >= bytes) return LBM_OK;
         if (stage) {
@@ -562,21 +573,28 @@ extern "C" int lbm_moments(lbm_ctx* c, double* rho, double* ux, double* uy) {
     const size_t n = (size_t)c->nx * c->ny, bytes = n * sizeof(double);
     double* outs[3] = {rho, ux, uy};
     double* dv[3] = {nullptr, nullptr, nullptr};
+    double* mapped[3] = {nullptr, nullptr, nullptr};
     bool st[3] = {false, false, false};
     size_t need = 0;
+    bool host = false;
     for (int i = 0; i < 3; ++i)
         if (outs[i]) {
             cudaPointerAttributes at{};
             cudaError_t e = cudaPointerGetAttributes(&at, outs[i]);
             if (e != cudaSuccess) cudaGetLastError();
-            if (!(e == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)))
-                need += bytes;
+            if (!(e == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged))) {
+                host = true;
+                mapped[i] = lbm_ctx::mapped_host(outs[i]);
+                if (!mapped[i]) need += bytes;
+            }
         }
     int rc = c->ensure_stage(need);
     if (rc) return rc;
     size_t off = 0;
     for (int i = 0; i < 3; ++i)
-        if (outs[i]) {
+        if (outs[i] && mapped[i]) {
+            dv[i] = mapped[i];
+        } else if (outs[i]) {
             dv[i] = c->device_view(outs[i], bytes, off, &st[i]);
             if (st[i]) off += bytes;
         }
@@ -584,7 +602,7 @@ extern "C" int lbm_moments(lbm_ctx* c, double* rho, double* ux, double* uy) {
     for (int i = 0; i < 3 && !rc; ++i)
         if (outs[i] && st[i])
             rc = c->cuda(cudaMemcpyAsync(outs[i], dv[i], bytes, cudaMemcpyDeviceToHost, c->stream), "moments copy");
-    if (!rc && need) rc = c->sync();
+    if (!rc && host) rc = c->sync();
     return rc;
 }
 
@@ -596,17 +614,34 @@ extern "C" int lbm_set_moments_ex(lbm_ctx* c, const double* rho, const double* u
     if (!c || !rho || !ux || !uy) return c ? c->fail(LBM_EINVAL, "NULL field") : LBM_EINVAL;
     if (flags & ~LBM_INIT_NEQ) return c->fail(LBM_EINVAL, "unknown lbm_set_moments_ex flag");
     const size_t bytes = (size_t)c->nx * c->ny * sizeof(double);
-    int rc = c->ensure_stage(3 * bytes);
-    if (rc) return rc;
     const double* ins[3] = {rho, ux, uy};
+    double* mapped[3];
+    size_t need = 0;
+    for (int i = 0; i < 3; ++i) {
+        mapped[i] = lbm_ctx::mapped_host(ins[i]);
+        cudaPointerAttributes at{};
+        const cudaError_t e = cudaPointerGetAttributes(&at, ins[i]);
+        if (e != cudaSuccess) cudaGetLastError();
+        const bool dev = e == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+        if (!dev && !mapped[i]) need += bytes;
+    }
+    int rc = c->ensure_stage(need);
+    if (rc) return rc;
     double* dv[3];
     size_t off = 0;
+    bool host = false;  // a host buffer the caller may reuse once this returns
     for (int i = 0; i < 3 && !rc; ++i) {
+        if (mapped[i]) {
+            dv[i] = mapped[i];
+            host = true;
+            continue;
+        }
         bool staged = false;
         dv[i] = c->device_view(ins[i], bytes, off, &staged);
         if (staged) {
             rc = c->cuda(cudaMemcpyAsync(dv[i], ins[i], bytes, cudaMemcpyHostToDevice, c->stream), "moments upload");
             off += bytes;
+            host = true;
         }
     }
     if (rc) return rc;
@@ -625,7 +660,7 @@ extern "C" int lbm_set_moments_ex(lbm_ctx* c, const double* rho, const double* u
     if (!rc)
         rc = c->cuda(launch_set_moments(c->dtype, c->cur(), dv[0], dv[1], dv[2], c->snap,
                                         (flags & LBM_INIT_NEQ) ? c->tau : 0.0, c->stream), "set_moments launch");
-    if (!rc && off) rc = c->sync();  // the staged host input may be reused after return
+    if (!rc && host) rc = c->sync();  // the host input may be reused after return
     return rc;
 }
 

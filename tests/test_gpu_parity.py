@@ -210,6 +210,36 @@ def test_set_moments_keeps_graphs_and_matches_a_fresh_context():
     assert torch.isfinite(s0).all()
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32s", "q16s"])
+def test_moments_through_pinned_host_buffers_equal_the_device_path(dtype):
+    """lbm_set_moments from, and lbm_moments into, page-locked host buffers (read and written by the
+    kernels over the host link) give bitwise what device buffers give."""
+    nx, ny = 200, 130
+    st = torch.cuda.current_stream().cuda_stream
+    r = uniform(5, (3, ny, nx))
+    seed = [1 + 0.01 * r[0], 0.05 * r[1], 0.05 * r[2]]
+    out = []
+    for pinned in (False, True):
+        ctx = B.lbm_create(nx, ny, 300.0, 0.1, dtype)
+        try:
+            B.lbm_set_stream(ctx, st)
+            if pinned:
+                src = [torch.tensor(a).pin_memory() for a in seed]
+                dst = [torch.full((ny, nx), float("nan"), dtype=torch.float64).pin_memory() for _ in range(3)]
+            else:
+                src = [torch.tensor(a, device="cuda") for a in seed]
+                dst = [torch.full((ny, nx), float("nan"), dtype=torch.float64, device="cuda") for _ in range(3)]
+            B.lbm_set_moments(ctx, *src)
+            B.lbm_step(ctx, 150)
+            B.lbm_moments(ctx, *dst)
+            torch.cuda.synchronize()
+            out.append([d.cpu() for d in dst])
+        finally:
+            B.lbm_destroy(ctx)
+    for a, b in zip(*out):
+        assert torch.isfinite(a).all() and torch.equal(a, b)
+
+
 @pytest.mark.parametrize("dtype,tol", [("f64", 1e-13), ("f32s", 3e-7), ("f32", 3e-7), ("f16s", 2e-3)])
 def test_set_moments_neq_matches_oracle(dtype, tol):
     """LBM_INIT_NEQ: f^eq plus (1 - 1/tau) times the first-order Chapman-Enskog part, on
