@@ -51,7 +51,7 @@ def cavity_list(nx, res, ars, U, extra_pairs=()):
     return cases
 
 
-def run_batched(cases, dtype, tol, max_steps, every, cap, tune_steps=50, save_series=None):
+def run_batched(cases, dtype, tol, max_steps, every, cap, tune_steps=50, save_series=None, shape=-1):
     st = torch.cuda.current_stream()
     b = B.lbm_batch_create([c["nx"] for c in cases], [c["ny"] for c in cases], [c["Re"] for c in cases],
                            [c["U"] for c in cases], dtype)
@@ -63,7 +63,9 @@ def run_batched(cases, dtype, tol, max_steps, every, cap, tune_steps=50, save_se
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         tune = None
-        if tune_steps > 0:
+        if shape >= 0:
+            B.lbm_batch_set_shape(b, shape)
+        elif tune_steps > 0:
             chosen, ms = B.lbm_batch_autotune(b, tune_steps)
             tune = {"chosen": chosen, "trial_ms": ms.tolist(), "steps": tune_steps}
         rc, done = B.lbm_batch_run_to_residual(b, len(cases), tol, max_steps)
@@ -150,6 +152,7 @@ def main(argv=None):
     ap.add_argument("--also-run-to-residual", action="store_true",
                     help="time the one-at-a-time arm a second time through lbm_run_to_residual")
     ap.add_argument("--autotune-steps", type=int, default=50, help="steps per tile-shape trial (0: keep the default shape)")
+    ap.add_argument("--shape", type=int, default=-1, help="use this tile shape (0..LBM_BATCH_SHAPES-1) instead of autotuning")
     ap.add_argument("--save-series", default=None, help="write the probe series of the batched arm (.npz)")
     ap.add_argument("--paper-pairs", action="store_true",
                     help="add every (Ar, Re) at which Sec. 3.3 reports a state (Table 3, Figs. 8-10)")
@@ -162,7 +165,7 @@ def main(argv=None):
     doc = {"nx": a.nx, "U": a.u, "dtype": a.dtype, "tol": a.tol, "max_steps": a.max_steps,
            "n_cavities": len(cases), "nodes": sum(c["nx"] * c["ny"] for c in cases)}
     doc["batched"] = run_batched(cases, a.dtype, a.tol, a.max_steps, a.probe_every, cap, a.autotune_steps,
-                                 a.save_series)
+                                 a.save_series, a.shape)
     if a.sequential:
         doc["sequential"] = run_sequential(cases, a.dtype, a.tol, a.max_steps)
         doc["speedup_time_to_steady"] = doc["sequential"]["wall_s"] / doc["batched"]["wall_s"]
