@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) k_batch(const BatchArgs a
                 const int y = rg * a.rows + r;
                 if (y >= cd.ny) break;
                 if (lane == 0 && (r == a.rows - 1 || y + 1 == cd.ny)) next = atomicAdd(&st->claim, 1u);
-                step_row<S, SHIFTED, REDUCE, V, HINT>(src, dst, cv, lane, x0, y, snap, pr,
+                step_row<S, SHIFTED, REDUCE, V, HINT, (sizeof(S) < 4)>(src, dst, cv, lane, x0, y, snap, pr,
                                                    [step]() { return step + 1; }, a0, a1, a2);
             }
             if constexpr (REDUCE) {

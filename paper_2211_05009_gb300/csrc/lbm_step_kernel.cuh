@@ -374,7 +374,9 @@ struct CavityView {
 // collision or wall closure, optional Eq. 6 accumulation and probe sampling, store.
 // step_time() = global index of the step being produced (called only when a probe sits in this
 // segment).
-template <typename S, bool SHIFTED, bool REDUCE, int V, int HINT, typename Probes, typename TimeFn>
+// EDGE_ALWAYS: run every warp through the node code with the wall tests instead of giving
+// all-interior warps their own copy (the batch kernel's choice for 16-bit storage, below).
+template <typename S, bool SHIFTED, bool REDUCE, int V, int HINT, bool EDGE_ALWAYS, typename Probes, typename TimeFn>
 __device__ __forceinline__ void step_row(const S* __restrict__ src, S* __restrict__ dst,
                                          const CavityView<typename St<S>::C>& cv, int lane, int x0,
                                          int y, typename St<S>::C* snap, const Probes& probes,
@@ -404,9 +406,10 @@ __device__ __forceinline__ void step_row(const S* __restrict__ src, S* __restric
     // Per node.  EDGE = false: every segment of the warp is interior (no wall, lid or padding
     // node), the case of all but the first and last warps of a row, so the wall tests compile
     // away; the arithmetic is the same either way.  The choice is made per warp (a per-lane choice
-    // would run both copies of the node code in a warp that holds a wall lane).  Only 4- and
-    // 8-byte storage takes the split: for 16-bit storage the kernel is issue-bound and the second
-    // copy of the node code measured slower.
+    // would run both copies of the node code in a warp that holds a wall lane).  With EDGE_ALWAYS
+    // there is one copy: the batch kernel's 16-bit instantiations measured faster that way (half
+    // the warps of a 500-wide cavity hold a wall lane; 45-cavity batch, f16s 131.4 -> 135.3 GLUPS),
+    // while the single-cavity 16-bit kernel gains from the split (4096^2 f16s 171.4 -> 177.6).
     auto node = [&](auto edge_c, int i) {
         constexpr bool EDGE = decltype(edge_c)::value;
         const int x = x0 + i;
@@ -490,7 +493,7 @@ __device__ __forceinline__ void step_row(const S* __restrict__ src, S* __restric
             }
         }
     };
-    if (sizeof(S) < 4 || __any_sync(kFull, (y == 0) | (y == ny - 1) | (x0 == 0) | (x0 + V >= nx))) {
+    if (EDGE_ALWAYS || __any_sync(kFull, (y == 0) | (y == ny - 1) | (x0 == 0) | (x0 + V >= nx))) {
 #pragma unroll
         for (int i = 0; i < V; ++i) node(std::true_type{}, i);
     } else {
@@ -580,7 +583,7 @@ __global__ void __launch_bounds__(32 * BY, (kStepMinBlocks<S, BY>)) k_step(const
     for (int r = 0; r < R; ++r) {
         const int y = yb + r;
         if (y >= a.ny) break;  // uniform across the warp
-        step_row<S, SHIFTED, REDUCE, V, HINT>(
+        step_row<S, SHIFTED, REDUCE, V, HINT, kIsQ16<S>>(
             src, dst, cv, lane, x0, y, static_cast<C*>(a.snap), ProbeList{a.probes},
             [&]() { return a.state->base + a.s + 1; }, acc_drho, acc_num, acc_den);
     }
